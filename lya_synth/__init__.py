@@ -1,0 +1,132 @@
+"""Seeded synthetic skewer fields (input generation only).
+
+This module feeds BOTH the FP64 oracle and the CUDA path with identical FP32
+inputs.  It holds none of the optical-depth arithmetic: it only draws a
+Gaussian random field per skewer and derives the three input arrays the
+method consumes (1+delta, the peculiar velocity, and a stored temperature).
+
+Recipe (stands in for the paper's simulated boxes, Sec. 2.1-2.2 and Sec. 4):
+  * skewer ``i`` of a field with seed ``s`` draws its Fourier amplitudes from
+    ``np.random.default_rng(SeedSequence([s, i]))``, so any subset of skewers
+    is reproducible on its own;
+  * 1D linear power P(k) ~ k^-1 exp(-(k/k_J)^2) on the modes k_n = 2 pi n / L,
+    n = 1 .. N/2-1 (k = 0 and the Nyquist mode are zero), scaled so that
+    sum_n P(k_n) = sigma_delta^2 (the ensemble variance of delta);
+  * the linear velocity of Eq. 3 in one dimension, v_k = i f aH delta_k / k
+    with f = 1 and aH = H(z)/(1+z) in km/s per h^-1 Mpc;
+  * the lognormal density 1+delta = exp(delta - sigma_delta^2/2), which stands
+    in for the paper's rank-ordered mapping to a hydrodynamical simulation;
+  * a stored temperature T = T0 (1+delta)^(gamma-1) (no pivot: the pivot is
+    applied by the method itself in its power-law mode).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, replace
+
+import numpy as np
+
+
+@dataclass(frozen=True)
+class FieldSpec:
+    """One family of seeded skewers.  Lengths in h^-1 Mpc, k in h Mpc^-1."""
+    n_pix: int
+    box: float
+    z: float
+    k_j: float
+    sigma_delta: float
+    T0: float
+    gamma: float
+    seed: int
+    h: float = 0.72
+    omega_m: float = 0.26
+    omega_l: float = 0.74
+
+    def with_(self, **kw) -> "FieldSpec":
+        return replace(self, **kw)
+
+
+def hubble_velocity_per_length(spec: FieldSpec) -> float:
+    """aH in km/s per comoving h^-1 Mpc, used to scale the linear velocity."""
+    e = np.sqrt(spec.omega_m * (1.0 + spec.z) ** 3 + spec.omega_l)
+    return 100.0 * e / (1.0 + spec.z)
+
+
+def _power(spec: FieldSpec) -> tuple[np.ndarray, np.ndarray]:
+    n = np.arange(1, spec.n_pix // 2, dtype=np.float64)
+    k = 2.0 * np.pi * n / spec.box
+    p = np.exp(-(k / spec.k_j) ** 2) / k
+    p *= spec.sigma_delta ** 2 / p.sum()
+    return k, p
+
+
+def gaussian_modes(spec: FieldSpec, ids) -> np.ndarray:
+    """Unit complex normal amplitudes, one row per skewer id, seeded per id."""
+    ids = np.asarray(ids, dtype=np.int64).ravel()
+    m = spec.n_pix // 2 - 1
+    out = np.empty((ids.size, m), dtype=np.complex128)
+    for row, sid in enumerate(ids):
+        rng = np.random.default_rng(np.random.SeedSequence([int(spec.seed), int(sid)]))
+        g = rng.standard_normal(2 * m)
+        out[row].real = g[:m]
+        out[row].imag = g[m:]
+    return out
+
+
+def skewers(spec: FieldSpec, ids, with_temp: bool = True, chunk: int = 4096):
+    """FP32 arrays (rho = 1+delta, vpec [km/s], temp [K] or None), shape [len(ids)][N]."""
+    ids = np.asarray(ids, dtype=np.int64).ravel()
+    N = spec.n_pix
+    if N < 4 or N % 2:
+        raise ValueError("n_pix must be even and >= 4")
+    k, p = _power(spec)
+    amp = np.sqrt(p)
+    ah = hubble_velocity_per_length(spec)
+    rho = np.empty((ids.size, N), dtype=np.float32)
+    vpec = np.empty((ids.size, N), dtype=np.float32)
+    temp = np.empty((ids.size, N), dtype=np.float32) if with_temp else None
+    for lo in range(0, ids.size, chunk):
+        sub = ids[lo:lo + chunk]
+        z = gaussian_modes(spec, sub)
+        X = np.zeros((sub.size, N // 2 + 1), dtype=np.complex128)
+        # delta(x) = sum_n (a_n cos k_n x + b_n sin k_n x), a, b ~ N(0, P_n)
+        X[:, 1:N // 2] = 0.5 * N * np.conj(z) * amp
+        delta = np.fft.irfft(X, n=N, axis=1)
+        V = np.zeros_like(X)
+        V[:, 1:N // 2] = 1j * ah * X[:, 1:N // 2] / k
+        v = np.fft.irfft(V, n=N, axis=1)
+        r = np.exp(delta - 0.5 * spec.sigma_delta ** 2)
+        rho[lo:lo + sub.size] = r
+        vpec[lo:lo + sub.size] = v
+        if with_temp:
+            temp[lo:lo + sub.size] = spec.T0 * r ** (spec.gamma - 1.0)
+    return rho, vpec, temp
+
+
+def random_subset(n_total: int, n_pick: int, seed: int) -> np.ndarray:
+    """Sorted random subset of skewer ids (without replacement)."""
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(n_total, size=min(n_pick, n_total), replace=False))
+
+
+# ---- the workloads of the paper's scale (names say what they are) ----------
+# 64 x 256 px, 20 h^-1 Mpc box at z = 2.5: the oracle finishes it in seconds.
+TINY_20MPC = FieldSpec(n_pix=256, box=20.0, z=2.5, k_j=10.0, sigma_delta=1.0,
+                       T0=1.5e4, gamma=1.5, seed=0)
+TINY_20MPC_SKEWERS = 64
+TINY_20MPC_FT = 0.80
+
+# 65,536 x 4,096 px from a periodic 1 h^-1 Gpc box at z = 2.5 (pixel 0.244
+# h^-1 Mpc, near the Jeans scale), the scale of the paper's large volumes.
+GPC_4096 = FieldSpec(n_pix=4096, box=1000.0, z=2.5, k_j=4.0, sigma_delta=1.5,
+                     T0=1.5e4, gamma=1.5, seed=1)
+GPC_4096_SKEWERS = 65536
+GPC_4096_FT = 0.80
+GPC_4096_ORACLE_SUBSET = (256, 1001)       # (count, rng seed)
+GPC_4096_PRECISION_SUBSET = (1024, 1002)
+
+# Rows along the contiguous axis of a periodic 1536^3 grid, 1 h^-1 Gpc box at z = 2.3.
+GRID_1536 = FieldSpec(n_pix=1536, box=1000.0, z=2.3, k_j=4.0, sigma_delta=1.5,
+                      T0=2.0e4, gamma=1.4, seed=4)
+GRID_1536_ROWS = 1536 * 1536
+GRID_1536_FT = 0.78
+GRID_1536_ORACLE_SUBSET = (512, 1004)
