@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark of the Lyman-alpha optical-depth hot path on GB300.
+
+One step = one pass of the whole path over the 65,536 x 4,096-pixel skewer
+field of a periodic 1 h^-1 Gpc box at z = 2.5 (stored temperature,
+gamma = 1.5, target <F> = 0.80): optical depth of every skewer (Eq. 4-6),
+the mean-flux root-find and F = exp(-A tau) (Sec. 2.3), and the flux
+statistics (Sec. 5.2).  The metric is output pixels per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+``value`` is timed with CUDA events on the launching stream with the inputs
+resident in HBM (3.2 GB of inputs, far above the 129 MB L2, so no flush is
+needed between steps); ``e2e`` repeats the step through the public API with
+the inputs copied from pinned host memory and F copied back every step.
+Under torchrun each rank runs an independent replica of the workload (weak
+scaling); rank 0 prints one JSON line with the max-over-ranks time.
+``--impl reference`` times the FP64 CPU oracle on the host cores on bounded
+samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import lya_synth as ls  # noqa: E402
+
+METRIC = "tau-skewer pixels/s on 1 GB300 at |dF|<=1e-5 vs FP64 oracle"
+UNIT = "pixels/s"
+WORKLOAD = "gpc_box_65536x4096_z2.5"
+ALG_BYTES_PER_PX = 16          # rho, vpec, T read (12 B) + tau written (4 B)
+
+
+def workload_config(spec, S, extra=None):
+    c = {"workload": WORKLOAD, "n_skewers": S, "n_pix": spec.n_pix, "box_mpc_h": spec.box,
+         "z": spec.z, "T": "stored", "gamma": spec.gamma, "target_mean_flux": ls.GPC_4096_FT,
+         "precision": "f32 pairs, compensated sum; f64 root-find",
+         "l2": "inputs 3.2 GB > 129 MB L2: no flush between steps"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_sample_run(spec, ids, rho, v, t):
+    import oracle
+    p = oracle.Params(box=spec.box, z=spec.z, t_mode=0)
+    t0 = time.perf_counter()
+    tau = oracle.tau(p, rho, v, t)
+    A, _ = oracle.rescale(tau, ls.GPC_4096_FT)
+    F = oracle.flux(tau, A)
+    oracle.flux_stats(F)
+    return time.perf_counter() - t0
+
+
+def oracle_timing(spec, seconds: float, seed: int = 7):
+    """Time the oracle on a sample sized to take about `seconds`."""
+    import oracle
+    oracle.build()
+    cores = oracle.num_threads()
+    rng = np.random.default_rng(seed)
+    n = cores
+    ids = np.sort(rng.choice(ls.GPC_4096_SKEWERS, n, replace=False))
+    r, v, t = ls.skewers(spec, ids)
+    dt = oracle_sample_run(spec, ids, r, v, t)
+    n2 = int(max(cores, min(4096, round(seconds / max(dt, 1e-3) * n / cores) * cores)))
+    ids = np.sort(rng.choice(ls.GPC_4096_SKEWERS, n2, replace=False))
+    r, v, t = ls.skewers(spec, ids)
+    dt = oracle_sample_run(spec, ids, r, v, t)
+    px = n2 * spec.n_pix
+    return {"value": px / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n2} random skewers x {spec.n_pix} px of the workload (full O(N^2) FP64 sum, "
+                      f"rescale to <F>=0.80, stats) in {dt:.1f} s"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    spec = ls.GPC_4096
+    import oracle
+    oracle.build()
+    cores = oracle.num_threads()
+    rng = np.random.default_rng(1234)
+    per_step = max(cores, 2 * cores)
+    times, px = [], 0
+    for step in range(args.warmup + args.steps):
+        ids = np.sort(rng.choice(ls.GPC_4096_SKEWERS, per_step, replace=False))
+        r, v, t = ls.skewers(spec, ids)
+        dt = oracle_sample_run(spec, ids, r, v, t)
+        if step >= args.warmup:
+            times.append(dt)
+            px += per_step * spec.n_pix
+    total = sum(times)
+    value = px / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(spec, ls.GPC_4096_SKEWERS,
+                                                           {"sample_per_step": f"{per_step} skewers"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} random skewers x {spec.n_pix} px per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    spec = ls.GPC_4096
+    S = ls.GPC_4096_SKEWERS if args.skewers is None else args.skewers
+    # host generation first: the spawn pool starts before any CUDA call
+    rho, v, t = ls.skewers_parallel(spec, np.arange(S))
+    import torch
+    world, rank, local = dist_setup()
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1105_4747_gb300 as lya
+
+    stream = torch.cuda.current_stream()
+    field = lya.Field(rho, v, t, box=spec.box, z=spec.z)
+    params = lya.ExtractParams(t_mode=0, precision=lya.PREC_F32_COMPENSATED)
+    tau = torch.empty((S, spec.n_pix), dtype=torch.float32, device="cuda")
+    F = torch.empty_like(tau)
+    n_px = S * spec.n_pix
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        lya.extract_skewers(field, params, out=tau)
+        if ev is not None:
+            ev[1].record(stream)
+        A, _ = lya.rescale_mean_flux(tau, ls.GPC_4096_FT, flux_out=F)
+        st = lya.flux_stats(F)
+        return A, st
+
+    for _ in range(args.warmup):
+        A, st = step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    tau_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = lya.kernel_launches()
+    start.record(stream)
+    for k in range(args.steps):
+        A, st = step(tau_ev[k])
+    end.record(stream)
+    end.synchronize()
+    launches = lya.kernel_launches() - launches0
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms = start.elapsed_time(end) / args.steps
+    ms = max_over_ranks(ms, world)
+    tau_ms = statistics.mean(a.elapsed_time(b) for a, b in tau_ev)
+
+    # end to end through the public API: host inputs in, host flux out
+    e2e = None
+    if not args.no_e2e:
+        rho_h = torch.from_numpy(rho).pin_memory()
+        v_h = torch.from_numpy(v).pin_memory()
+        t_h = torch.from_numpy(t).pin_memory()
+        F_h = torch.empty((S, spec.n_pix), dtype=torch.float32).pin_memory()
+
+        def e2e_step():
+            field.load(rho_h, v_h, t_h)
+            lya.extract_skewers(field, params, out=tau)
+            lya.rescale_mean_flux(tau, ls.GPC_4096_FT, flux_out=F)
+            lya.flux_stats(F)
+            F_h.copy_(F, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n_e2e = max(1, min(args.steps, 5))
+        e0.record(stream)
+        for _ in range(n_e2e):
+            e2e_step()
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1) / n_e2e, world)
+        e2e = {"value": world * n_px / (e2e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": 3 * n_px * 4, "d2h_bytes_per_step": n_px * 4,
+               "ms_per_step": e2e_ms, "steps": n_e2e}
+        del rho_h, v_h, t_h, F_h
+
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    achieved = ALG_BYTES_PER_PX * n_px / (tau_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "tau_kernel<0>", "kernel_ms": tau_ms,
+                "peak_source": "measured" if peaks else "fallback",
+                "alg_bytes_per_launch": ALG_BYTES_PER_PX * n_px}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_timing(spec, args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": world * n_px / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": workload_config(spec, S, {"parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                                                    "A": A, "mean_flux": st.mean_flux}),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+    field.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--skewers", type=int, default=None, help="fewer skewers (debug only)")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,190 @@
+/*
+ * lya.h -- C ABI of the GB300 Lyman-alpha optical-depth library (liblya.so).
+ *
+ * The library extracts H I optical depth along skewers through a gridded
+ * density / velocity / temperature field and turns it into transmitted flux,
+ * following the semi-analytic method of Greig, Bolton & Wyithe (2011):
+ *
+ *   Eq. 5   T = T0 (1+delta)^(gamma-1), held at T(1+delta = 10) above the
+ *           pivot (power-law mode), or T read per pixel (stored mode);
+ *   Eq. 4   n_HI ~ (T/1e4)^-0.7 (1+delta)^2 (fluctuating Gunn-Peterson);
+ *   Eq. 6   tau(i) = (c sigma_a dR / sqrt(pi)) sum_j n_HI(j)/b(j)
+ *                    exp(-((v_H(i) - u(j))/b(j))^2),  b = sqrt(2 k T/m_H),
+ *           u(j) = v_H(j) + v_pec(j), summed periodically along the skewer;
+ *   Sec 2.3 F = exp(-A tau) with A solved so that <F> hits a target;
+ *   Sec 5.2 flux statistics: <F>, Var F, tau_eff = -ln<F>, 21-bin PDF.
+ *
+ * Conventions shared by every entry point:
+ *   - Arrays are FP32, row-major [n_skewers][n_pix]: one skewer is n_pix
+ *     contiguous floats.  Velocities are km/s, temperatures K, lengths
+ *     h^-1 Mpc (comoving).  "rho" is 1 + delta_b (density over the mean).
+ *   - "Device" pointers are CUDA global-memory pointers on the current
+ *     device; "host" pointers are ordinary (preferably pinned) memory.
+ *   - stream is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     are stream-ordered; a call that returns a host value (A, statistics)
+ *     synchronises that stream before returning.
+ *   - Every call returns a lya_status.  No C++ exception crosses the ABI.
+ *     Arguments are validated on the host before any launch; an invalid
+ *     argument returns LYA_EINVAL and launches nothing.
+ *   - The caller owns every buffer it passes in; a field owns (or, when
+ *     borrowed, references) its device arrays until lya_destroy_field.
+ */
+#ifndef LYA_H
+#define LYA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LYA_OK = 0,
+    LYA_EINVAL = -1,     /* bad argument, or a field value outside its domain */
+    LYA_ENOMEM = -2,     /* a device allocation failed                        */
+    LYA_ECUDA = -3,      /* a CUDA runtime call failed                        */
+    LYA_ENOCONV = -4,    /* the mean-flux root-find did not converge / no root */
+    LYA_ETIMEDOUT = -5,  /* a bounded device wait gave up                     */
+    LYA_EBUDGET = -6,    /* a request does not fit the memory budget          */
+    LYA_EDEVICE = -7     /* no usable sm_103 device                           */
+} lya_status;
+
+/* Opaque handle to a field resident in device memory. */
+typedef struct lya_field_s* lya_field;
+
+/* Geometry and cosmology of a field (defaults: the paper's cosmology, Sec. 2:
+ * h = 0.72, Omega_m = 0.26, Omega_L = 0.74, Omega_b = 0.0444). */
+typedef struct {
+    double box;          /* comoving skewer length, h^-1 Mpc (> 0)            */
+    double z;            /* redshift of the spectra (> -1)                     */
+    double h, omega_m, omega_l, omega_b;
+    double y_he;         /* helium mass fraction in nbar_H of Eq. 4 (0.24)     */
+    int64_t n_skewers;   /* >= 1                                              */
+    int64_t n_pix;       /* pixels per skewer, 16 <= n_pix <= 8192, even      */
+    int has_temp;        /* 1: the field carries a temperature array          */
+} lya_field_desc;
+
+/* Source of the arrays passed to lya_create_field / lya_field_load. */
+enum {
+    LYA_SRC_HOST = 0,          /* host memory: copied to the device            */
+    LYA_SRC_DEVICE_COPY = 1,   /* device memory: copied into field-owned memory */
+    LYA_SRC_DEVICE_BORROW = 2  /* device memory: referenced, not copied; the
+                                  caller keeps it alive and unchanged while the
+                                  field exists (create only)                   */
+};
+
+/* Accumulation precision of the pair sum (Eq. 6). */
+enum {
+    LYA_PREC_F32_COMPENSATED = 0, /* FP32 pairs, compensated (Kahan) sum       */
+    LYA_PREC_F32_NAIVE = 1,       /* FP32 pairs, plain FP32 sum                 */
+    LYA_PREC_F64 = 2              /* FP64 throughout (comparator; n_pix <= 4096) */
+};
+
+/* Per-extraction physics (Eq. 4-6). */
+typedef struct {
+    int t_mode;          /* 0: stored T (field must have one); 1: Eq. 5 power law */
+    double T0;           /* K, power-law mode                                  */
+    double gamma;        /* power-law slope, power-law mode                    */
+    double delta_pivot;  /* 1+delta above which T is constant (10; INFINITY = off) */
+    double gamma12;      /* H I photo-ionisation rate / 1e-12 s^-1 (> 0)       */
+    double nsigma;       /* pairs with |v_H(i)-u(j)| <= nsigma b(j) are summed (8) */
+    int precision;       /* LYA_PREC_*                                         */
+} lya_extract_params;
+
+typedef struct {
+    double mean_flux;    /* <F>                                               */
+    double var_flux;     /* population variance of F                          */
+    double tau_eff;      /* -ln <F>                                           */
+    int64_t pdf[21];     /* bin k counts (2k-1)/40 <= F < (2k+1)/40 (Sec. 5.2) */
+    int64_t n;           /* number of values                                  */
+} lya_flux_stats_t;
+
+/*
+ * Create a field of desc->n_skewers skewers x desc->n_pix pixels (Sec. 2.3:
+ * the gridded density, peculiar velocity and temperature the spectra are
+ * drawn from).  rho = 1+delta (>= 0, finite), vpec in km/s (finite), temp in
+ * K (> 0 where rho > 0; NULL iff desc->has_temp == 0).  src is LYA_SRC_*.
+ * The field validates every value once on the device and records the largest
+ * temperature (it bounds the line width).  Returns LYA_EINVAL for a bad
+ * descriptor or an out-of-domain value, LYA_ENOMEM if device memory runs out.
+ */
+lya_status lya_create_field(const lya_field_desc* desc, const float* rho,
+                            const float* vpec, const float* temp, int src,
+                            void* stream, lya_field* out);
+
+/*
+ * Overwrite the arrays of an owned field with new values of the same shape
+ * (src = LYA_SRC_HOST or LYA_SRC_DEVICE_COPY), validating them as above.
+ * Stream-ordered; synchronises the stream to read the validation result.
+ */
+lya_status lya_field_load(lya_field field, const float* rho, const float* vpec,
+                          const float* temp, int src, void* stream);
+
+/* Release a field (waits for work on the device to finish first). */
+lya_status lya_destroy_field(lya_field field);
+
+/*
+ * Read and clear the field's device error word (set by lya_extract_skewers
+ * when a skewer id is out of range).  Synchronises the stream; returns
+ * LYA_EINVAL if an extraction since the last call saw a bad id.
+ */
+lya_status lya_field_status(lya_field field, void* stream);
+
+/* Shape of a field. */
+lya_status lya_field_shape(lya_field field, int64_t* n_skewers, int64_t* n_pix);
+
+/*
+ * Optical depth along skewers (Eq. 4-6): tau_out[r][i] for the skewers
+ * skewer_ids[r], r < n_ids (a DEVICE array of int64 in [0, n_skewers); NULL
+ * means all skewers in order, with n_ids == n_skewers).  tau_out is a device
+ * array of n_ids * n_pix floats, owned by the caller.  The sum is periodic
+ * over the skewer and keeps every pair with |v_H(i) - u(j)| <= nsigma b(j)
+ * (a superset of them is allowed).  Out-of-range ids are not checked on the
+ * host; the kernel writes zeros for them and returns LYA_EINVAL at the next
+ * synchronising call on the field.
+ */
+lya_status lya_extract_skewers(lya_field field, const lya_extract_params* params,
+                               const int64_t* skewer_ids, int64_t n_ids,
+                               float* tau_out, void* stream);
+
+/*
+ * Mean-flux rescaling (Sec. 2.3): find A with <exp(-A tau)> = target over all
+ * n device values tau (every pixel of every skewer, equally weighted).
+ * Safeguarded Newton in FP64 from A0 = -ln(target)/<tau>, stopping when
+ * |<exp(-A tau)> - target| <= tol or the step stalls at FP64 resolution.
+ * *A_out receives A (host).  If flux_out (device, n floats) is not NULL it
+ * receives F = exp(-A tau).  Returns LYA_EINVAL if target is not in (0,1),
+ * tau holds a negative or non-finite value or all tau are 0; LYA_ENOCONV if
+ * no A reaches the target (too many tau = 0) or max_iter is exhausted.
+ * Synchronises the stream.
+ */
+lya_status lya_rescale_mean_flux(const float* tau, int64_t n, double target,
+                                 double tol, int max_iter, double* A_out,
+                                 float* flux_out, void* stream);
+
+/*
+ * Flux statistics (Sec. 2.3, Sec. 5.2) over n device values F: mean,
+ * population variance, tau_eff = -ln<F> and the 21-bin PDF with bin k holding
+ * (2k-1)/40 <= F < (2k+1)/40 (clamped to [0, 20]); the bin decision is exact
+ * for FP32 F.  Synchronises the stream.
+ */
+lya_status lya_flux_stats(const float* flux, int64_t n, lya_flux_stats_t* out,
+                          void* stream);
+
+/* Human-readable text of a status code (static storage). */
+const char* lya_strerror(lya_status status);
+
+/*
+ * Number of kernels this library has launched in the process so far (a
+ * monotone counter; diagnostics for benchmarks).
+ */
+uint64_t lya_kernel_launches(void);
+
+/* Version string of the library build. */
+const char* lya_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LYA_H */

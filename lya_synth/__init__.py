@@ -130,3 +130,36 @@ GRID_1536 = FieldSpec(n_pix=1536, box=1000.0, z=2.3, k_j=4.0, sigma_delta=1.5,
 GRID_1536_ROWS = 1536 * 1536
 GRID_1536_FT = 0.78
 GRID_1536_ORACLE_SUBSET = (512, 1004)
+
+
+def _skewers_chunk(args):
+    spec, ids, with_temp = args
+    return skewers(spec, ids, with_temp=with_temp)
+
+
+def skewers_parallel(spec: FieldSpec, ids, with_temp: bool = True, workers: int | None = None,
+                     chunk: int = 2048):
+    """Same arrays as :func:`skewers`, generated by a spawn-started process pool.
+
+    Start it before the first CUDA call of the process (spawn keeps the
+    workers free of any CUDA state either way).
+    """
+    import multiprocessing as mp
+    import os
+    ids = np.asarray(ids, dtype=np.int64).ravel()
+    workers = workers or max(1, min(16, (os.cpu_count() or 1)))
+    if workers == 1 or ids.size <= chunk:
+        return skewers(spec, ids, with_temp=with_temp)
+    N = spec.n_pix
+    rho = np.empty((ids.size, N), dtype=np.float32)
+    vpec = np.empty((ids.size, N), dtype=np.float32)
+    temp = np.empty((ids.size, N), dtype=np.float32) if with_temp else None
+    jobs = [(spec, ids[lo:lo + chunk], with_temp) for lo in range(0, ids.size, chunk)]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        for k, (r, v, t) in enumerate(pool.imap(_skewers_chunk, jobs)):
+            lo = k * chunk
+            rho[lo:lo + r.shape[0]] = r
+            vpec[lo:lo + r.shape[0]] = v
+            if with_temp:
+                temp[lo:lo + r.shape[0]] = t
+    return rho, vpec, temp

@@ -1,0 +1,25 @@
+"""GB300-native Lyman-alpha optical depth along skewers.
+
+The data-parallel hot path of the semi-analytic Lyman-alpha forest method of
+Greig, Bolton & Wyithe (2011): fluctuating Gunn-Peterson n_HI (Eq. 4-5), the
+thermal Doppler profile summed periodically into tau(u_i) (Eq. 6), the
+mean-flux rescaling F = exp(-A tau) (Sec. 2.3) and the flux statistics of
+Sec. 5.2.  Every step runs in the hand-written sm_103a kernels of
+``liblya.so``; this package only marshals arguments through its C ABI
+(``include/lya.h``).  PyTorch provides device memory and streams.
+"""
+from ._binding import (  # noqa: F401
+    PREC_F32_COMPENSATED,
+    PREC_F32_NAIVE,
+    PREC_F64,
+    ExtractParams,
+    Field,
+    FluxStats,
+    LyaError,
+    extract_skewers,
+    flux_stats,
+    kernel_launches,
+    library_path,
+    load_library,
+    rescale_mean_flux,
+)

@@ -1,0 +1,285 @@
+"""ctypes binding of liblya.so: argument marshalling only.
+
+Names mirror the C ABI in ``include/lya.h``.  Device buffers are torch CUDA
+tensors; host buffers are numpy arrays (or CPU tensors).  Nothing here
+computes any part of the method, and nothing falls back to the CPU: if the
+library is not built or there is no CUDA device, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "liblya.so")
+_lock = threading.Lock()
+_lib = None
+
+LYA_OK, LYA_EINVAL, LYA_ENOMEM, LYA_ECUDA, LYA_ENOCONV, LYA_ETIMEDOUT, LYA_EBUDGET, LYA_EDEVICE = \
+    0, -1, -2, -3, -4, -5, -6, -7
+SRC_HOST, SRC_DEVICE_COPY, SRC_DEVICE_BORROW = 0, 1, 2
+PREC_F32_COMPENSATED, PREC_F32_NAIVE, PREC_F64 = 0, 1, 2
+
+
+class LyaError(RuntimeError):
+    """A liblya call returned a status other than LYA_OK."""
+
+    def __init__(self, status: int, what: str):
+        self.status = status
+        msg = load_library().lya_strerror(status).decode()
+        super().__init__(f"{what}: {msg} (status {status})")
+
+
+class _FieldDesc(ctypes.Structure):
+    _fields_ = [("box", ctypes.c_double), ("z", ctypes.c_double), ("h", ctypes.c_double),
+                ("omega_m", ctypes.c_double), ("omega_l", ctypes.c_double),
+                ("omega_b", ctypes.c_double), ("y_he", ctypes.c_double),
+                ("n_skewers", ctypes.c_int64), ("n_pix", ctypes.c_int64),
+                ("has_temp", ctypes.c_int)]
+
+
+class _ExtractParams(ctypes.Structure):
+    _fields_ = [("t_mode", ctypes.c_int), ("T0", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("delta_pivot", ctypes.c_double), ("gamma12", ctypes.c_double),
+                ("nsigma", ctypes.c_double), ("precision", ctypes.c_int)]
+
+
+class _FluxStats(ctypes.Structure):
+    _fields_ = [("mean_flux", ctypes.c_double), ("var_flux", ctypes.c_double),
+                ("tau_eff", ctypes.c_double), ("pdf", ctypes.c_int64 * 21), ("n", ctypes.c_int64)]
+
+
+def kernel_launches() -> int:
+    """Kernels liblya has launched in this process (lya_kernel_launches)."""
+    return int(load_library().lya_kernel_launches())
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load_library():
+    """Load liblya.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"{_LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "(nvcc, sm_103a); there is no CPU fallback")
+        lib = ctypes.CDLL(_LIB_PATH)
+        vp, i64, i32, d = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        lib.lya_strerror.argtypes = [i32]
+        lib.lya_strerror.restype = ctypes.c_char_p
+        lib.lya_version.argtypes = []
+        lib.lya_version.restype = ctypes.c_char_p
+        lib.lya_kernel_launches.argtypes = []
+        lib.lya_kernel_launches.restype = ctypes.c_uint64
+        lib.lya_create_field.argtypes = [ctypes.POINTER(_FieldDesc), vp, vp, vp, i32, vp, ctypes.POINTER(vp)]
+        lib.lya_field_load.argtypes = [vp, vp, vp, vp, i32, vp]
+        lib.lya_destroy_field.argtypes = [vp]
+        lib.lya_field_status.argtypes = [vp, vp]
+        lib.lya_field_shape.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        lib.lya_extract_skewers.argtypes = [vp, ctypes.POINTER(_ExtractParams), vp, i64, vp, vp]
+        lib.lya_rescale_mean_flux.argtypes = [vp, i64, d, d, i32, ctypes.POINTER(d), vp, vp]
+        lib.lya_flux_stats.argtypes = [vp, i64, ctypes.POINTER(_FluxStats), vp]
+        for name in ("lya_create_field", "lya_field_load", "lya_destroy_field", "lya_field_status",
+                     "lya_field_shape", "lya_extract_skewers", "lya_rescale_mean_flux", "lya_flux_stats"):
+            getattr(lib, name).restype = i32
+        _lib = lib
+        return lib
+
+
+def _check(status: int, what: str):
+    if status != LYA_OK:
+        raise LyaError(status, what)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _require_cuda_f32(t, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError(f"{name} must be contiguous float32")
+    return t
+
+
+@dataclass
+class ExtractParams:
+    """Physics of one extraction (Eq. 4-6); see lya_extract_params in include/lya.h."""
+    t_mode: int = 0
+    T0: float = 1.5e4
+    gamma: float = 1.5
+    delta_pivot: float = 10.0
+    gamma12: float = 1.0
+    nsigma: float = 8.0
+    precision: int = PREC_F32_COMPENSATED
+
+    def _c(self) -> _ExtractParams:
+        return _ExtractParams(int(self.t_mode), float(self.T0), float(self.gamma),
+                              float(self.delta_pivot), float(self.gamma12), float(self.nsigma),
+                              int(self.precision))
+
+
+class Field:
+    """A skewer field resident in device memory (lya_create_field).
+
+    ``rho`` (1+delta), ``vpec`` (km/s) and ``temp`` (K, optional) are either
+    numpy arrays / CPU tensors (copied from the host) or CUDA tensors (copied,
+    or referenced when ``borrow=True``), shaped [n_skewers][n_pix], float32.
+    """
+
+    def __init__(self, rho, vpec, temp=None, *, box: float, z: float, h: float = 0.72,
+                 omega_m: float = 0.26, omega_l: float = 0.74, omega_b: float = 0.0444,
+                 y_he: float = 0.24, borrow: bool = False, stream=None):
+        lib = load_library()
+        torch = _torch()
+        self._handle = None
+        self._keep = None
+        arrays, src = self._marshal(rho, vpec, temp, borrow)
+        S, N = arrays[0].shape
+        desc = _FieldDesc(box, z, h, omega_m, omega_l, omega_b, y_he, S, N, 1 if temp is not None else 0)
+        out = ctypes.c_void_p()
+        ptrs = [self._ptr(a) for a in arrays]
+        _check(lib.lya_create_field(ctypes.byref(desc), ptrs[0], ptrs[1], ptrs[2], src,
+                                    _stream_handle(stream) if torch.cuda.is_available() else None,
+                                    ctypes.byref(out)), "lya_create_field")
+        self._handle = out
+        self.n_skewers, self.n_pix = S, N
+        self.has_temp = temp is not None
+        self.box, self.z = box, z
+        if src == SRC_DEVICE_BORROW:
+            self._keep = arrays          # the field references these tensors
+
+    @staticmethod
+    def _marshal(rho, vpec, temp, borrow):
+        torch = _torch()
+        if isinstance(rho, torch.Tensor) and rho.is_cuda:
+            arrs = [_require_cuda_f32(rho, "rho"), _require_cuda_f32(vpec, "vpec"),
+                    None if temp is None else _require_cuda_f32(temp, "temp")]
+            src = SRC_DEVICE_BORROW if borrow else SRC_DEVICE_COPY
+        else:
+            if borrow:
+                raise ValueError("borrow=True needs CUDA tensors")
+            conv = [None if a is None else np.ascontiguousarray(
+                a.numpy() if isinstance(a, torch.Tensor) else a, dtype=np.float32) for a in (rho, vpec, temp)]
+            arrs = conv
+            src = SRC_HOST
+        if arrs[0].ndim != 2 or tuple(arrs[1].shape) != tuple(arrs[0].shape) or (
+                arrs[2] is not None and tuple(arrs[2].shape) != tuple(arrs[0].shape)):
+            raise ValueError("rho, vpec and temp must share a 2-D shape [n_skewers][n_pix]")
+        return arrs, src
+
+    @staticmethod
+    def _ptr(a):
+        if a is None:
+            return None
+        if isinstance(a, np.ndarray):
+            return a.ctypes.data
+        return a.data_ptr()
+
+    def load(self, rho, vpec, temp=None, stream=None):
+        """Overwrite the field's arrays (lya_field_load)."""
+        arrays, src = self._marshal(rho, vpec, temp, False)
+        ptrs = [self._ptr(a) for a in arrays]
+        _check(load_library().lya_field_load(self._handle, ptrs[0], ptrs[1], ptrs[2], src,
+                                             _stream_handle(stream)), "lya_field_load")
+
+    def status(self, stream=None):
+        """Raise if an extraction saw an out-of-range skewer id (lya_field_status)."""
+        _check(load_library().lya_field_status(self._handle, _stream_handle(stream)), "lya_field_status")
+
+    @property
+    def handle(self):
+        return self._handle
+
+    def close(self):
+        if self._handle:
+            load_library().lya_destroy_field(self._handle)
+            self._handle = None
+            self._keep = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def extract_skewers(field: Field, params: ExtractParams, ids=None, out=None, stream=None):
+    """tau [n_ids][n_pix] on the device (lya_extract_skewers).
+
+    ``ids``: None (all skewers) or an int64 tensor / array of skewer ids.
+    """
+    torch = _torch()
+    lib = load_library()
+    if ids is None:
+        n_ids, ids_ptr = field.n_skewers, None
+    else:
+        ids_t = torch.as_tensor(ids, dtype=torch.int64).to("cuda").contiguous()
+        n_ids, ids_ptr = ids_t.numel(), ids_t.data_ptr()
+    if out is None:
+        out = torch.empty((n_ids, field.n_pix), dtype=torch.float32, device="cuda")
+    else:
+        _require_cuda_f32(out, "out")
+        if out.numel() != n_ids * field.n_pix:
+            raise ValueError("out has the wrong size")
+    p = params._c()
+    _check(lib.lya_extract_skewers(field.handle, ctypes.byref(p), ids_ptr, n_ids,
+                                   out.data_ptr() if n_ids else None, _stream_handle(stream)),
+           "lya_extract_skewers")
+    if ids is not None:
+        out._lya_ids = ids_t            # keep the id buffer alive until the kernel ran
+    return out
+
+
+def rescale_mean_flux(tau, target: float, tol: float = 1e-12, max_iter: int = 50,
+                      flux_out=True, stream=None):
+    """Mean-flux rescaling (lya_rescale_mean_flux): returns (A, F or None)."""
+    torch = _torch()
+    _require_cuda_f32(tau, "tau")
+    F = None
+    if flux_out is True:
+        F = torch.empty_like(tau)
+    elif flux_out is not None and flux_out is not False:
+        F = _require_cuda_f32(flux_out, "flux_out")
+    A = ctypes.c_double(math.nan)
+    _check(load_library().lya_rescale_mean_flux(tau.data_ptr(), tau.numel(), float(target), float(tol),
+                                                int(max_iter), ctypes.byref(A),
+                                                F.data_ptr() if F is not None else None,
+                                                _stream_handle(stream)), "lya_rescale_mean_flux")
+    return A.value, F
+
+
+@dataclass
+class FluxStats:
+    mean_flux: float
+    var_flux: float
+    tau_eff: float
+    pdf: np.ndarray
+    n: int
+
+
+def flux_stats(flux, stream=None) -> FluxStats:
+    """<F>, Var F, tau_eff, 21-bin PDF of device flux values (lya_flux_stats)."""
+    _require_cuda_f32(flux, "flux")
+    out = _FluxStats()
+    _check(load_library().lya_flux_stats(flux.data_ptr(), flux.numel(), ctypes.byref(out),
+                                         _stream_handle(stream)), "lya_flux_stats")
+    return FluxStats(out.mean_flux, out.var_flux, out.tau_eff, np.array(out.pdf[:], dtype=np.int64), out.n)

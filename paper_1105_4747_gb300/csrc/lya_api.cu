@@ -1,0 +1,305 @@
+// lya_api.cu -- the C ABI of liblya.so (declared in include/lya.h).
+//
+// Host side of the library: argument validation, field ownership, the FP64
+// physical constants of Eq. 4-6, and the launches.  Every step of the
+// computation runs in the CUDA kernels of tau_extract.cu and mean_flux.cu.
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include "lya.h"
+#include "lya_internal.h"
+
+namespace {
+
+// ---- physical constants (cgs) and the paper's values -------------------------
+constexpr double kC = 2.99792458e10;          // speed of light, cm/s
+constexpr double kSigmaA = 4.48e-18;          // Ly-alpha cross-section, cm^2 (Sec. 2.3)
+constexpr double kBoltz = 1.380649e-16;       // erg/K
+constexpr double kMH = 1.6735575e-24;         // hydrogen atom mass, g
+constexpr double kMpc = 3.0856775814913673e24;// cm
+constexpr double kGrav = 6.67430e-8;          // cm^3 g^-1 s^-2
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kLog2e = 1.4426950408889634;
+
+struct Physics {
+    double du;      // pixel velocity width, km/s
+    double K;       // tau_i = K sum_j w_j 2^-(c_j d_ij)^2 with w_j = rho^2 (T/1e4)^-1.2
+    double b1e4;    // Doppler parameter at 1e4 K, km/s
+};
+
+// Eq. 4 and Eq. 6 with the cosmology of the field, in FP64.
+Physics physics(const lya_field_desc& d, double gamma12)
+{
+    Physics p;
+    const double zp = 1.0 + d.z;
+    const double hz = 100.0 * d.h * std::sqrt(d.omega_m * zp * zp * zp + d.omega_l);  // km/s/Mpc
+    const double dR_mpc = d.box / (d.h * zp * (double)d.n_pix);                      // proper Mpc
+    p.du = hz * dR_mpc;
+    const double dR_cm = dR_mpc * kMpc;
+    const double h0 = 100.0 * d.h * 1.0e5 / kMpc;                                    // s^-1
+    const double rho_crit = 3.0 * h0 * h0 / (8.0 * kPi * kGrav);
+    const double nbar_h = (1.0 - d.y_he) * d.omega_b * rho_crit * zp * zp * zp / kMH;
+    const double q = zp / 4.0;
+    // n_HI(T, rho) = n_coef (T/1e4)^-0.7 rho^2     (Eq. 4)
+    const double n_coef = 7.24e-6 * nbar_h * (d.omega_b * d.h * d.h / 0.024) / gamma12 * q * q * q;
+    p.b1e4 = std::sqrt(2.0 * kBoltz * 1.0e4 / kMH) / 1.0e5;                           // km/s
+    // Eq. 6: (c sigma dR / sqrt(pi)) n_HI / b_cgs, with b = b1e4 (T/1e4)^0.5
+    p.K = kC * kSigmaA * dR_cm / std::sqrt(kPi) * n_coef / (p.b1e4 * 1.0e5);
+    return p;
+}
+
+bool desc_ok(const lya_field_desc* d)
+{
+    if (!d) return false;
+    if (!(d->box > 0.0) || !std::isfinite(d->box)) return false;
+    if (!(d->z > -1.0) || !std::isfinite(d->z)) return false;
+    if (!(d->h > 0.0) || !(d->omega_m >= 0.0) || !(d->omega_l >= 0.0) || !(d->omega_b > 0.0)) return false;
+    if (!(d->omega_m * (1.0 + d->z) * (1.0 + d->z) * (1.0 + d->z) + d->omega_l > 0.0)) return false;
+    if (!(d->y_he >= 0.0 && d->y_he < 1.0)) return false;
+    if (d->n_skewers < 1 || d->n_pix < 16 || d->n_pix > 8192 || (d->n_pix & 1)) return false;
+    if (d->has_temp != 0 && d->has_temp != 1) return false;
+    return true;
+}
+
+lya_status from_cuda(cudaError_t e)
+{
+    if (e == cudaSuccess) return LYA_OK;
+    if (e == cudaErrorMemoryAllocation) return LYA_ENOMEM;
+    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver || e == cudaErrorNoKernelImageForDevice)
+        return LYA_EDEVICE;
+    return LYA_ECUDA;
+}
+
+}  // namespace
+
+namespace lya {
+static std::atomic<uint64_t> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+uint64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace lya
+
+struct lya_field_s {
+    lya_field_desc desc;
+    float* rho = nullptr;
+    float* vpec = nullptr;
+    float* temp = nullptr;
+    bool owned = false;
+    int* d_err = nullptr;            // device error word of extract launches
+    lya::FieldCheck* d_check = nullptr;
+    float temp_max = 0.f;
+    int device = 0;
+};
+
+namespace {
+
+lya_status check_and_record(lya_field f, cudaStream_t s)
+{
+    const int64_t n = f->desc.n_skewers * f->desc.n_pix;
+    cudaError_t e = lya::launch_field_check(f->rho, f->vpec, f->temp, n, f->d_check, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    lya::FieldCheck h{};
+    e = cudaMemcpyAsync(&h, f->d_check, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (h.bad_rho || h.bad_vpec || h.bad_temp) return LYA_EINVAL;
+    std::memcpy(&f->temp_max, &h.temp_max_bits, sizeof(float));
+    return LYA_OK;
+}
+
+lya_status copy_in(lya_field f, const float* rho, const float* vpec, const float* temp, int src,
+                   cudaStream_t s)
+{
+    const size_t bytes = sizeof(float) * (size_t)(f->desc.n_skewers * f->desc.n_pix);
+    const cudaMemcpyKind kind = src == LYA_SRC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    cudaError_t e = cudaMemcpyAsync(f->rho, rho, bytes, kind, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f->vpec, vpec, bytes, kind, s);
+    if (e == cudaSuccess && f->temp) e = cudaMemcpyAsync(f->temp, temp, bytes, kind, s);
+    return from_cuda(e);
+}
+
+void release(lya_field f)
+{
+    if (!f) return;
+    if (f->owned) {
+        cudaFree(f->rho);
+        cudaFree(f->vpec);
+        cudaFree(f->temp);
+    }
+    cudaFree(f->d_err);
+    cudaFree(f->d_check);
+    delete f;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lya_strerror(lya_status s)
+{
+    switch (s) {
+    case LYA_OK: return "success";
+    case LYA_EINVAL: return "invalid argument or out-of-domain field value";
+    case LYA_ENOMEM: return "out of device memory";
+    case LYA_ECUDA: return "CUDA runtime error";
+    case LYA_ENOCONV: return "mean-flux root-find did not converge (or no root exists)";
+    case LYA_ETIMEDOUT: return "bounded device wait timed out";
+    case LYA_EBUDGET: return "request exceeds the memory budget";
+    case LYA_EDEVICE: return "no usable sm_103 CUDA device";
+    }
+    return "unknown status";
+}
+
+const char* lya_version(void) { return "lya 0.1 (sm_103a)"; }
+
+uint64_t lya_kernel_launches(void) { return lya::launches_so_far(); }
+
+lya_status lya_create_field(const lya_field_desc* desc, const float* rho, const float* vpec,
+                            const float* temp, int src, void* stream, lya_field* out)
+{
+    if (!out) return LYA_EINVAL;
+    *out = nullptr;
+    if (!desc_ok(desc) || !rho || !vpec) return LYA_EINVAL;
+    if ((desc->has_temp != 0) != (temp != nullptr)) return LYA_EINVAL;
+    if (src != LYA_SRC_HOST && src != LYA_SRC_DEVICE_COPY && src != LYA_SRC_DEVICE_BORROW) return LYA_EINVAL;
+    if (desc->n_skewers > INT64_MAX / desc->n_pix) return LYA_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    lya_field f = new (std::nothrow) lya_field_s();
+    if (!f) return LYA_ENOMEM;
+    f->desc = *desc;
+    cudaGetDevice(&f->device);
+    const size_t bytes = sizeof(float) * (size_t)(desc->n_skewers * desc->n_pix);
+    cudaError_t e = cudaMalloc((void**)&f->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(f->d_err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&f->d_check, sizeof(lya::FieldCheck));
+    if (e != cudaSuccess) { release(f); return from_cuda(e); }
+    if (src == LYA_SRC_DEVICE_BORROW) {
+        f->owned = false;
+        f->rho = const_cast<float*>(rho);
+        f->vpec = const_cast<float*>(vpec);
+        f->temp = const_cast<float*>(temp);
+    } else {
+        f->owned = true;
+        e = cudaMalloc((void**)&f->rho, bytes);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&f->vpec, bytes);
+        if (e == cudaSuccess && temp) e = cudaMalloc((void**)&f->temp, bytes);
+        if (e != cudaSuccess) { release(f); return from_cuda(e); }
+        lya_status st = copy_in(f, rho, vpec, temp, src, s);
+        if (st != LYA_OK) { release(f); return st; }
+    }
+    lya_status st = check_and_record(f, s);
+    if (st != LYA_OK) { release(f); return st; }
+    *out = f;
+    return LYA_OK;
+}
+
+lya_status lya_field_load(lya_field f, const float* rho, const float* vpec, const float* temp, int src,
+                          void* stream)
+{
+    if (!f || !rho || !vpec || !f->owned) return LYA_EINVAL;
+    if ((f->temp != nullptr) != (temp != nullptr)) return LYA_EINVAL;
+    if (src != LYA_SRC_HOST && src != LYA_SRC_DEVICE_COPY) return LYA_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    lya_status st = copy_in(f, rho, vpec, temp, src, s);
+    if (st != LYA_OK) return st;
+    return check_and_record(f, s);
+}
+
+lya_status lya_destroy_field(lya_field f)
+{
+    if (!f) return LYA_EINVAL;
+    cudaError_t e = cudaDeviceSynchronize();
+    release(f);
+    return from_cuda(e);
+}
+
+lya_status lya_field_shape(lya_field f, int64_t* n_skewers, int64_t* n_pix)
+{
+    if (!f) return LYA_EINVAL;
+    if (n_skewers) *n_skewers = f->desc.n_skewers;
+    if (n_pix) *n_pix = f->desc.n_pix;
+    return LYA_OK;
+}
+
+lya_status lya_field_status(lya_field f, void* stream)
+{
+    if (!f) return LYA_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, f->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f->d_err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return from_cuda(e);
+    return h ? LYA_EINVAL : LYA_OK;
+}
+
+lya_status lya_extract_skewers(lya_field f, const lya_extract_params* p, const int64_t* ids, int64_t n_ids,
+                               float* tau_out, void* stream)
+{
+    if (!f || !p) return LYA_EINVAL;
+    if (n_ids < 0 || (n_ids > 0 && !tau_out)) return LYA_EINVAL;
+    if (!ids && n_ids != f->desc.n_skewers) return LYA_EINVAL;
+    if (n_ids > 0x7fffffffLL) return LYA_EINVAL;
+    if (p->t_mode != 0 && p->t_mode != 1) return LYA_EINVAL;
+    if (p->t_mode == 0 && !f->temp) return LYA_EINVAL;
+    if (p->t_mode == 1) {
+        if (!(p->T0 > 0.0) || !std::isfinite(p->T0) || !std::isfinite(p->gamma)) return LYA_EINVAL;
+        if (!(p->delta_pivot > 0.0)) return LYA_EINVAL;
+    }
+    if (!(p->gamma12 > 0.0) || !std::isfinite(p->gamma12)) return LYA_EINVAL;
+    if (!(p->nsigma >= 1.0 && p->nsigma <= 40.0)) return LYA_EINVAL;
+    if (p->precision < LYA_PREC_F32_COMPENSATED || p->precision > LYA_PREC_F64) return LYA_EINVAL;
+    const int N = (int)f->desc.n_pix;
+    if (lya::tau_smem_bytes(N, p->precision) > lya::max_dynamic_smem()) return LYA_EINVAL;
+
+    const Physics ph = physics(f->desc, p->gamma12);
+    lya::TauLaunch L{};
+    L.rho = f->rho;
+    L.vpec = f->vpec;
+    L.temp = p->t_mode == 0 ? f->temp : nullptr;
+    L.ids = ids;
+    L.n_rows = n_ids;
+    L.n_skewers = f->desc.n_skewers;
+    L.n_pix = N;
+    L.tau_out = tau_out;
+    L.err = f->d_err;
+    L.t_mode = p->t_mode;
+    L.du_hi = (float)ph.du;
+    L.du_lo = (float)(ph.du - (double)L.du_hi);
+    L.inv_du = (float)(1.0 / ph.du);
+    L.c_coef = (float)(std::sqrt(kLog2e) / ph.b1e4);
+    L.h_coef = (float)(p->nsigma * std::sqrt(kLog2e));
+    L.K = (float)ph.K;
+    L.T0 = (float)p->T0;
+    L.gm1 = (float)(p->gamma - 1.0);
+    L.pivot = std::isfinite(p->delta_pivot) ? (float)p->delta_pivot : INFINITY;
+    L.du_d = ph.du;
+    L.inv_du_d = 1.0 / ph.du;
+    L.c_coef_d = std::sqrt(kLog2e) / ph.b1e4;
+    L.h_coef_d = p->nsigma * std::sqrt(kLog2e);
+    L.K_d = ph.K;
+    L.T0_d = p->T0;
+    L.gm1_d = p->gamma - 1.0;
+    L.pivot_d = p->delta_pivot;
+    return from_cuda(lya::launch_tau(L, p->precision, static_cast<cudaStream_t>(stream)));
+}
+
+lya_status lya_rescale_mean_flux(const float* tau, int64_t n, double target, double tol, int max_iter,
+                                 double* A_out, float* flux_out, void* stream)
+{
+    if (!tau || n <= 0 || !A_out) return LYA_EINVAL;
+    if (!(target > 0.0 && target < 1.0)) return LYA_EINVAL;
+    if (!(tol > 0.0) || max_iter < 1) return LYA_EINVAL;
+    return lya::mean_flux_solve(tau, n, target, tol, max_iter, A_out, flux_out,
+                                static_cast<cudaStream_t>(stream));
+}
+
+lya_status lya_flux_stats(const float* flux, int64_t n, lya_flux_stats_t* out, void* stream)
+{
+    if (!flux || n <= 0 || !out) return LYA_EINVAL;
+    return lya::flux_stats_run(flux, n, out, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,71 @@
+// lya_internal.h -- host/device structures passed from the C-ABI layer to the
+// kernel launchers.  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lya.h"
+
+namespace lya {
+
+// Everything the optical-depth kernel needs, precomputed in FP64 on the host
+// and handed to the device in both FP32 and FP64 forms.
+struct TauLaunch {
+    const float* rho;
+    const float* vpec;
+    const float* temp;        // nullptr in power-law mode
+    const int64_t* ids;       // nullptr: row r is skewer r
+    int64_t n_rows;           // skewers to extract (grid size)
+    int64_t n_skewers;        // skewers in the field (id bound)
+    int n_pix;
+    float* tau_out;           // [n_rows][n_pix]
+    int* err;                 // device error word: bit 0 = skewer id out of range
+
+    int t_mode;               // 0 stored T, 1 power law (Eq. 5)
+    // FP32 forms
+    float du_hi, du_lo;       // pixel velocity width as a double-float (km/s)
+    float inv_du;             // 1/du
+    float c_coef;             // sqrt(log2 e) / b(1e4 K), s/km
+    float h_coef;             // nsigma * sqrt(log2 e): window half-width = h_coef / a
+    float K;                  // Eq. 6 prefactor times Eq. 4 constants (see api)
+    float T0, gm1, pivot;     // power law: T = T0 min(rho, pivot)^gm1
+    // FP64 forms (the FP64 comparator kernel)
+    double du_d, inv_du_d, c_coef_d, h_coef_d, K_d, T0_d, gm1_d, pivot_d;
+};
+
+// Launch the optical-depth kernel for the requested precision.
+cudaError_t launch_tau(const TauLaunch& L, int precision, cudaStream_t stream);
+
+// Shared-memory bytes the optical-depth kernel needs for n_pix pixels.
+size_t tau_smem_bytes(int n_pix, int precision);
+
+// Maximum dynamic shared memory a block may opt into on this device.
+size_t max_dynamic_smem();
+
+// Mean-flux root-find (Sec. 2.3) over n device values of tau; writes A to
+// *A_out and, if flux_out is not null, F = exp(-A tau).  Returns a lya_status.
+lya_status mean_flux_solve(const float* tau, int64_t n, double target, double tol,
+                           int max_iter, double* A_out, float* flux_out,
+                           cudaStream_t stream);
+
+// Flux statistics (Sec. 2.3, 5.2) over n device flux values.
+lya_status flux_stats_run(const float* flux, int64_t n, lya_flux_stats_t* out,
+                          cudaStream_t stream);
+
+// Field validation: counts out-of-domain values and finds the largest T.
+struct FieldCheck {
+    unsigned long long bad_rho, bad_vpec, bad_temp;
+    unsigned int temp_max_bits;
+};
+cudaError_t launch_field_check(const float* rho, const float* vpec, const float* temp,
+                               int64_t n, FieldCheck* d_out, cudaStream_t stream);
+
+// Count one kernel launch (lya_kernel_launches).
+void count_launch(int n = 1);
+uint64_t launches_so_far();
+
+// Number of SMs of the current device (cached).
+int sm_count();
+
+}  // namespace lya
