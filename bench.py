@@ -74,7 +74,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -304,7 +304,7 @@ def run_ours(args):
     achieved = ALG_BYTES_PER_PX * n_px / (tau_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None,
-                "kernel": "tau_kernel<0>", "kernel_ms": tau_ms,
+                "kernel": "tau_env_kernel<0,8>", "kernel_ms": tau_ms,
                 "peak_source": "measured" if peaks else "fallback",
                 "alg_bytes_per_launch": ALG_BYTES_PER_PX * n_px}
 

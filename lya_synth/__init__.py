@@ -141,11 +141,13 @@ def skewers_parallel(spec: FieldSpec, ids, with_temp: bool = True, workers: int 
                      chunk: int = 2048):
     """Same arrays as :func:`skewers`, generated by a spawn-started process pool.
 
-    Start it before the first CUDA call of the process (spawn keeps the
-    workers free of any CUDA state either way).
+    Spawned workers re-import the caller's main module, so a script calling
+    this must keep its top-level work under ``if __name__ == "__main__":``.
+    A worker that dies raises BrokenProcessPool here instead of hanging.
     """
     import multiprocessing as mp
     import os
+    from concurrent.futures import ProcessPoolExecutor
     ids = np.asarray(ids, dtype=np.int64).ravel()
     workers = workers or max(1, min(16, (os.cpu_count() or 1)))
     if workers == 1 or ids.size <= chunk:
@@ -155,8 +157,8 @@ def skewers_parallel(spec: FieldSpec, ids, with_temp: bool = True, workers: int 
     vpec = np.empty((ids.size, N), dtype=np.float32)
     temp = np.empty((ids.size, N), dtype=np.float32) if with_temp else None
     jobs = [(spec, ids[lo:lo + chunk], with_temp) for lo in range(0, ids.size, chunk)]
-    with mp.get_context("spawn").Pool(workers) as pool:
-        for k, (r, v, t) in enumerate(pool.imap(_skewers_chunk, jobs)):
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        for k, (r, v, t) in enumerate(ex.map(_skewers_chunk, jobs)):
             lo = k * chunk
             rho[lo:lo + r.shape[0]] = r
             vpec[lo:lo + r.shape[0]] = v

@@ -89,7 +89,9 @@ struct lya_field_s {
     bool owned = false;
     int* d_err = nullptr;            // device error word of extract launches
     lya::FieldCheck* d_check = nullptr;
-    float temp_max = 0.f;
+    float temp_max = 0.f;            // largest T where rho > 0 (stored-T fields)
+    float rho_max = 0.f;             // largest rho
+    float rho_minpos = 0.f;          // smallest rho > 0
     int device = 0;
 };
 
@@ -106,6 +108,8 @@ lya_status check_and_record(lya_field f, cudaStream_t s)
     if (e != cudaSuccess) return from_cuda(e);
     if (h.bad_rho || h.bad_vpec || h.bad_temp) return LYA_EINVAL;
     std::memcpy(&f->temp_max, &h.temp_max_bits, sizeof(float));
+    std::memcpy(&f->rho_max, &h.rho_max_bits, sizeof(float));
+    std::memcpy(&f->rho_minpos, &h.rho_minpos_bits, sizeof(float));
     return LYA_OK;
 }
 
@@ -240,7 +244,7 @@ lya_status lya_extract_skewers(lya_field f, const lya_extract_params* p, const i
 {
     if (!f || !p) return LYA_EINVAL;
     if (n_ids < 0 || (n_ids > 0 && !tau_out)) return LYA_EINVAL;
-    if (!ids && n_ids != f->desc.n_skewers) return LYA_EINVAL;
+    if (!ids && n_ids != 0 && n_ids != f->desc.n_skewers) return LYA_EINVAL;
     if (n_ids > 0x7fffffffLL) return LYA_EINVAL;
     if (p->t_mode != 0 && p->t_mode != 1) return LYA_EINVAL;
     if (p->t_mode == 0 && !f->temp) return LYA_EINVAL;
@@ -252,9 +256,27 @@ lya_status lya_extract_skewers(lya_field f, const lya_extract_params* p, const i
     if (!(p->nsigma >= 1.0 && p->nsigma <= 40.0)) return LYA_EINVAL;
     if (p->precision < LYA_PREC_F32_COMPENSATED || p->precision > LYA_PREC_F64) return LYA_EINVAL;
     const int N = (int)f->desc.n_pix;
-    if (lya::tau_smem_bytes(N, p->precision) > lya::max_dynamic_smem()) return LYA_EINVAL;
-
     const Physics ph = physics(f->desc, p->gamma12);
+
+    // Largest temperature any source can have -> bound on the window half-width
+    // (pixels) of every line: nsigma b(T_max)/du + 1/2 (the residual), +1 margin.
+    double t_max;
+    if (p->t_mode == 0) {
+        t_max = f->temp_max;
+    } else {
+        const double piv = p->delta_pivot;
+        const double r_hi = std::fmin((double)f->rho_max, piv);
+        const double r_lo = std::fmin((double)f->rho_minpos, piv);
+        const double g1 = p->gamma - 1.0;
+        t_max = p->T0 * std::fmax(r_hi > 0 ? std::pow(r_hi, g1) : 0.0, r_lo > 0 ? std::pow(r_lo, g1) : 0.0);
+    }
+    const double b_max = ph.b1e4 * std::sqrt(std::fmax(t_max, 0.0) * 1e-4);
+    double w = std::floor(p->nsigma * b_max / ph.du + 0.5) + 1.0;
+    if (!(w >= 1.0)) w = 1.0;
+    const int w_cap = (N - 1) / 2;
+    const int w_max = w > (double)w_cap ? w_cap : (int)w;
+    if (lya::tau_smem_bytes(N, w_max, p->precision) > lya::max_dynamic_smem()) return LYA_EINVAL;
+
     lya::TauLaunch L{};
     L.rho = f->rho;
     L.vpec = f->vpec;
@@ -265,6 +287,7 @@ lya_status lya_extract_skewers(lya_field f, const lya_extract_params* p, const i
     L.n_pix = N;
     L.tau_out = tau_out;
     L.err = f->d_err;
+    L.w_max = w_max;
     L.t_mode = p->t_mode;
     L.du_hi = (float)ph.du;
     L.du_lo = (float)(ph.du - (double)L.du_hi);

@@ -95,4 +95,83 @@ __device__ inline int block_exclusive_scan(int* data, int n, int* warp_tot)
     return total;
 }
 
+// Inclusive warp scan with max (ascending lanes) or min (descending lanes).
+__device__ __forceinline__ int warp_scan_max(int v)
+{
+    const unsigned lane = threadIdx.x & 31u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= (unsigned)o) v = max(v, u);
+    }
+    return v;
+}
+__device__ __forceinline__ int warp_suffix_min(int v)
+{
+    const unsigned lane = threadIdx.x & 31u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int u = __shfl_down_sync(0xffffffffu, v, o);
+        if (lane + (unsigned)o < 32u) v = min(v, u);
+    }
+    return v;
+}
+
+// In-place inclusive prefix max of data[0..n) by the whole block.
+// warp_tmp holds >= 32 ints of shared scratch.  Contains __syncthreads().
+__device__ inline void block_prefix_max(int* data, int n, int* warp_tmp, int lowest)
+{
+    const int nt = blockDim.x, tid = threadIdx.x;
+    const int per = (n + nt - 1) / nt;
+    const int lo = min(n, tid * per), hi = min(n, lo + per);
+    int local = lowest;
+    for (int k = lo; k < hi; ++k) local = max(local, data[k]);
+    const int warp = tid >> 5, lane = tid & 31, nwarps = (nt + 31) >> 5;
+    int inc = warp_scan_max(local);
+    if (lane == 31) warp_tmp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < nwarps ? warp_tmp[lane] : lowest;
+        int wi = warp_scan_max(w);
+        int ex = __shfl_up_sync(0xffffffffu, wi, 1);
+        if (lane < nwarps) warp_tmp[lane] = lane ? ex : lowest;   // max over earlier warps
+    }
+    __syncthreads();
+    int ex_thread = __shfl_up_sync(0xffffffffu, inc, 1);
+    int run = max(warp_tmp[warp], lane ? ex_thread : lowest);
+    for (int k = lo; k < hi; ++k) {
+        run = max(run, data[k]);
+        data[k] = run;
+    }
+    __syncthreads();
+}
+
+// In-place inclusive suffix min of data[0..n) (data[k] = min data[k..n)).
+__device__ inline void block_suffix_min(int* data, int n, int* warp_tmp, int highest)
+{
+    const int nt = blockDim.x, tid = threadIdx.x;
+    const int per = (n + nt - 1) / nt;
+    const int lo = min(n, tid * per), hi = min(n, lo + per);
+    int local = highest;
+    for (int k = lo; k < hi; ++k) local = min(local, data[k]);
+    const int warp = tid >> 5, lane = tid & 31, nwarps = (nt + 31) >> 5;
+    int inc = warp_suffix_min(local);                 // min over this and later lanes
+    if (lane == 0) warp_tmp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < nwarps ? warp_tmp[lane] : highest;
+        int wi = warp_suffix_min(w);
+        int ex = __shfl_down_sync(0xffffffffu, wi, 1);
+        if (lane < nwarps) warp_tmp[lane] = (lane + 1 < nwarps) ? ex : highest;   // min over later warps
+    }
+    __syncthreads();
+    int ex_thread = __shfl_down_sync(0xffffffffu, inc, 1);
+    int run = min(warp_tmp[warp], lane < 31 ? ex_thread : highest);
+    for (int k = hi - 1; k >= lo; --k) {
+        run = min(run, data[k]);
+        data[k] = run;
+    }
+    __syncthreads();
+}
+
 }  // namespace lya

@@ -21,6 +21,7 @@ struct TauLaunch {
     int n_pix;
     float* tau_out;           // [n_rows][n_pix]
     int* err;                 // device error word: bit 0 = skewer id out of range
+    int w_max;                // bound on every source's window half-width, pixels (<= (n_pix-1)/2)
 
     int t_mode;               // 0 stored T, 1 power law (Eq. 5)
     // FP32 forms
@@ -37,8 +38,9 @@ struct TauLaunch {
 // Launch the optical-depth kernel for the requested precision.
 cudaError_t launch_tau(const TauLaunch& L, int precision, cudaStream_t stream);
 
-// Shared-memory bytes the optical-depth kernel needs for n_pix pixels.
-size_t tau_smem_bytes(int n_pix, int precision);
+// Shared-memory bytes the optical-depth kernel needs for n_pix pixels and a
+// window bound w_max (the kernel variant is chosen by what fits).
+size_t tau_smem_bytes(int n_pix, int w_max, int precision);
 
 // Maximum dynamic shared memory a block may opt into on this device.
 size_t max_dynamic_smem();
@@ -56,7 +58,9 @@ lya_status flux_stats_run(const float* flux, int64_t n, lya_flux_stats_t* out,
 // Field validation: counts out-of-domain values and finds the largest T.
 struct FieldCheck {
     unsigned long long bad_rho, bad_vpec, bad_temp;
-    unsigned int temp_max_bits;
+    unsigned int temp_max_bits;      // largest T where rho > 0 (float bits)
+    unsigned int rho_max_bits;       // largest rho (float bits)
+    unsigned int rho_minpos_bits;    // smallest rho > 0 (float bits; 0x7f800000 if none)
 };
 cudaError_t launch_field_check(const float* rho, const float* vpec, const float* temp,
                                int64_t n, FieldCheck* d_out, cudaStream_t stream);

@@ -287,12 +287,17 @@ __global__ void __launch_bounds__(kThreads) field_check_kernel(const float* __re
                                                              FieldCheck* out)
 {
     unsigned long long br = 0, bv = 0, bt = 0;
-    float tmax = 0.f;
+    float tmax = 0.f, rmax = 0.f, rmin = INFINITY;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const float r = rho[i], u = v[i];
-        br += !(r >= 0.f && isfinite(r));
+        const bool rok = r >= 0.f && isfinite(r);
+        br += !rok;
         bv += !(isfinite(u) && fabsf(u) < 2.99792458e5f);
+        if (rok && r > 0.f) {
+            rmax = fmaxf(rmax, r);
+            rmin = fminf(rmin, r);
+        }
         if (T) {
             const float t = T[i];
             const bool ok = isfinite(t) && (t > 0.f || !(r > 0.f));
@@ -305,12 +310,17 @@ __global__ void __launch_bounds__(kThreads) field_check_kernel(const float* __re
         bv += __shfl_down_sync(0xffffffffu, bv, o);
         bt += __shfl_down_sync(0xffffffffu, bt, o);
         tmax = fmaxf(tmax, __shfl_down_sync(0xffffffffu, tmax, o));
+        rmax = fmaxf(rmax, __shfl_down_sync(0xffffffffu, rmax, o));
+        rmin = fminf(rmin, __shfl_down_sync(0xffffffffu, rmin, o));
     }
     if ((threadIdx.x & 31) == 0) {
         if (br) atomicAdd(&out->bad_rho, br);
         if (bv) atomicAdd(&out->bad_vpec, bv);
         if (bt) atomicAdd(&out->bad_temp, bt);
-        atomicMax(&out->temp_max_bits, __float_as_uint(tmax));   // T >= 0: bit order = value order
+        // non-negative floats order like their bit patterns
+        atomicMax(&out->temp_max_bits, __float_as_uint(tmax));
+        atomicMax(&out->rho_max_bits, __float_as_uint(rmax));
+        atomicMin(&out->rho_minpos_bits, __float_as_uint(rmin));
     }
 }
 
@@ -346,7 +356,10 @@ size_t max_dynamic_smem()
 cudaError_t launch_field_check(const float* rho, const float* vpec, const float* temp, int64_t n,
                                FieldCheck* d_out, cudaStream_t stream)
 {
-    cudaError_t e = cudaMemsetAsync(d_out, 0, sizeof(FieldCheck), stream);
+    FieldCheck init{};
+    init.rho_minpos_bits = 0x7f800000u;     // +inf
+    cudaError_t e = cudaMemcpyAsync(d_out, &init, sizeof(FieldCheck), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);   // init is a stack value
     if (e != cudaSuccess || n == 0) return e;
     field_check_kernel<<<grid_for(n), kThreads, 0, stream>>>(rho, vpec, temp, n, d_out);
     count_launch();
