@@ -11,27 +11,30 @@
 
 namespace lya {
 
-// 2^x on the MUFU unit (PTX ex2.approx.f32; subnormal results are kept).
+// 2^x on the MUFU unit (PTX ex2.approx.ftz.f32).  Results below 2^-126
+// flush to zero: a line-profile term that small is ~1e-38 of its line's
+// weight, and a transmitted flux that small is 0 to any tolerance used here.
 __device__ __forceinline__ float ex2(float x)
 {
     float y;
-    asm("ex2.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
 
-// log2(x) on the MUFU unit (PTX lg2.approx.f32).
+// log2(x) on the MUFU unit (PTX lg2.approx.ftz.f32; x is a normal positive
+// temperature or density here).
 __device__ __forceinline__ float lg2(float x)
 {
     float y;
-    asm("lg2.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
 
-// 1/x on the MUFU unit (PTX rcp.approx.f32).
+// 1/x on the MUFU unit (PTX rcp.approx.ftz.f32).
 __device__ __forceinline__ float rcp_approx(float x)
 {
     float y;
-    asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
 

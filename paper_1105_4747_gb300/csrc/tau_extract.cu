@@ -1,20 +1,19 @@
 // tau_extract.cu -- optical depth along skewers (Eq. 4-6), sm_103a.
 //
-// One CTA owns one skewer.  The work per skewer is:
-//   1. histogram of target pixels: source j lands in bin t_j = j + s_j (mod N)
-//      with s_j = rint(v_j/du), the nearest pixel of u_j = v_H(j) + v_pec(j);
-//   2. block scan -> bin starts, then a scatter of per-source records
-//      {a_j, c_j r_j, w_j, j} into shared memory (a counting sort by target),
-//      and a per-bin insertion sort on j so the order inside a bin -- and
-//      with it the summation order -- does not depend on atomic timing;
-//   3. for each output pixel i, the windowed pair sum over the sources whose
-//      bins lie within W pixels of i (W = the skewer's largest
-//      ceil((nsigma b_j + |r_j|)/du)), periodic over the skewer.
+// One CTA owns one skewer.  Two kernels:
+//   * tau_scatter_kernel (FP32, the product path): every source adds its
+//     thermally broadened line to the pixels within nsigma Doppler widths
+//     of its target, accumulating in shared memory (compensated or plain);
+//   * tau_kernel (FP64 comparator): sources counting-sorted by target pixel,
+//     then each output pixel sums the sources of the bins within the
+//     skewer's widest reach.
 //
-// Velocity differences are formed in a local frame: with s_j integer and
-// r_j = v_j - s_j du (a double-float du keeps r_j exact to ~1 ulp), the
-// Gaussian argument is c_j ((i - t_j) du - r_j) with an exact integer pixel
-// offset, so FP32 never subtracts two velocities of size ~1e5 km/s.
+// Source j lands at the target pixel t_j = j + s_j (mod N), s_j = rint(v_j/du),
+// the pixel nearest u_j = v_H(j) + v_pec(j).  Velocity differences are formed
+// in a local frame: with s_j integer and r_j = v_j - s_j du (a double-float du
+// keeps r_j exact to ~1 ulp), the Gaussian argument is c_j (m du - r_j) with
+// an exact integer pixel offset m, so FP32 never subtracts two velocities of
+// size ~1e5 km/s.
 //
 // Per source (FP32, MUFU):  T_j = stored or T0 min(rho_j, pivot)^(gamma-1)
 //   w_j = rho_j^2 (T_j/1e4)^-1.2          (n_HI / b of Eq. 4 and Eq. 6 up to K)
@@ -56,10 +55,17 @@ template <> struct Prec<LYA_PREC_F64> {
     __device__ static double value(const Acc& a) { return a.s; }
 };
 
-__device__ __forceinline__ int wrap_pixel(int64_t x, int N)
+// x mod N in [0, N) for |x| < 2^30 (the host bounds |v_pec|/du below 2^29);
+// one wrap either way is a compare and an add, farther ones a division.
+__device__ __forceinline__ int wrap_pixel(int x, int N)
 {
-    int64_t r = x % N;
-    return (int)(r < 0 ? r + N : r);
+    if (x < 0) x += N;
+    else if (x >= N) x -= N;
+    if ((unsigned)x >= (unsigned)N) {
+        x %= N;
+        if (x < 0) x += N;
+    }
+    return x;
 }
 
 // ---- per-source preparation -------------------------------------------------
@@ -80,7 +86,7 @@ __device__ __forceinline__ SrcF32 prep_f32(const TauLaunch& L, float rho, float 
     const float sf = target_shift_f32(v, L);
     float r = fmaf(-sf, L.du_hi, v);                     // exact product inside the fma
     r = fmaf(-sf, L.du_lo, r);
-    s.t = wrap_pixel((int64_t)j + (int64_t)sf, L.n_pix);
+    s.t = wrap_pixel(j + (int)sf, L.n_pix);
     s.a = c * L.du_hi;
     s.bb = c * r;
     // |m du - r| <= nsigma b needs |m| <= (nsigma b + |r|)/du, and nsigma b/du =
@@ -103,7 +109,7 @@ __device__ __forceinline__ SrcF64 prep_f64(const TauLaunch& L, float rho_f, floa
     const double c = L.c_coef_d / sqrt(tt);
     const double sf = rint(v * L.inv_du_d);
     const double r = v - sf * L.du_d;
-    s.t = wrap_pixel((int64_t)j + (int64_t)sf, L.n_pix);
+    s.t = wrap_pixel(j + (int)sf, L.n_pix);
     s.a = c * L.du_d;
     s.bb = c * r;
     const double hx = (L.h_coef_d / s.a + fabs(r) * L.inv_du_d) * (1.0 + 1e-12);
@@ -172,8 +178,8 @@ __global__ void __launch_bounds__(512) tau_kernel(const TauLaunch L)
         if (r > 0.f) {
             const float v = vpec[j];
             int t;
-            if (PREC == LYA_PREC_F64) t = wrap_pixel((int64_t)j + (int64_t)rint((double)v * L.inv_du_d), N);
-            else t = wrap_pixel((int64_t)j + (int64_t)target_shift_f32(v, L), N);
+            if (PREC == LYA_PREC_F64) t = wrap_pixel(j + (int)rint((double)v * L.inv_du_d), N);
+            else t = wrap_pixel(j + (int)target_shift_f32(v, L), N);
             atomicAdd(&bin[t + 1], 1);
         }
     }
@@ -238,41 +244,68 @@ __global__ void __launch_bounds__(512) tau_kernel(const TauLaunch L)
     }
 }
 
-// ---- adaptive-window kernel -------------------------------------------------------
+// ---- scatter kernel (FP32) --------------------------------------------------------
 //
-// Each source j covers the output pixels |i - t_j| <= h_j.  Instead of one
-// window for the whole skewer, every output pixel i gets the tightest run of
-// target bins [L_i, R_i] that still contains every source covering it:
-//   L_i = first bin t with max_{t' <= t}(t' + h_t') >= i   (prefix max of right reach)
-//   R_i = last  bin t with min_{t' >= t}(t' - h_t') <= i   (suffix min of left reach)
-// computed on bins extended by w_max on both sides so the periodic wrap is
-// explicit.  The sources in [L_i, R_i] are a superset of the pairs with
-// |v_H(i) - u_j| <= nsigma b_j; outside the neighbourhood of the broadest
-// lines the run is ~2 h + 1 sources long.
+// One CTA owns one skewer and keeps its optical depth in shared memory.
+// Every source j adds its line, w_j 2^-(c_j (m du - r_j))^2, to the pixels
+// t_j + m, |m| <= h_j, where h_j = floor((nsigma b_j + |r_j|)/du) is the
+// exact reach of the nsigma b_j cut: the work is one MUFU ex2 and one
+// shared-memory atomic add per kept pair, with no sort and no window search.
 //
-// Shared memory: records (N) | bin starts (N+1) | aux (N ints: packed
-// target/half-width while sorting, then L_i and R_i as int16) | reach (N + 2 w_max).
-constexpr int kReachLow = -(1 << 28);
-constexpr int kReachHigh = 1 << 28;
+// The accumulator is extended by w_max pixels on each side, so a line that
+// crosses the periodic seam lands in a halo slot; the halo is folded back
+// onto the skewer before the write-out.
+//
+// Compensated variant: the add is an atomic that returns the old value, so
+// the thread knows exactly which FP32 addition the memory performed and
+// recovers its rounding error with TwoSum (old + v = s + e exactly); the
+// errors e go to a second array by plain atomic adds.  hi + lo equals the
+// exact sum of the terms up to O(n u^2), whatever order the atomics ran in.
+// Naive variant: one plain atomic add per pair.  In both, the order in which
+// atomics from different threads land is not fixed, so repeated runs agree
+// to the accumulation's rounding (the compensated one to ~1 ulp of tau), not
+// bit for bit.
+//
+// Shared memory: hi (N + 2 w_max floats) | lo (N + 2 w_max floats, compensated only).
 
-template <int PREC, int MAXQ>
-__global__ void __launch_bounds__(512) tau_env_kernel(const TauLaunch L)
+// Exact rounding error of s = fl(a + b): a + b = s + e (Knuth's TwoSum).
+__device__ __forceinline__ float two_sum_err(float a, float b, float s)
 {
-    using Rec = typename Prec<PREC>::Rec;
-    using Acc = typename Prec<PREC>::Acc;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int warp_tot[33];
+    const float bp = __fsub_rn(s, a);
+    const float ap = __fsub_rn(s, bp);
+    return __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
 
+template <bool COMP>
+__device__ __forceinline__ void scatter_add(float* hi, float* lo, int o, float v)
+{
+    if constexpr (COMP) {
+        const float old = atomicAdd(hi + o, v);
+        const float s = __fadd_rn(old, v);
+        const float e = two_sum_err(old, v, s);
+        if (e != 0.f) atomicAdd(lo + o, e);
+    } else {
+        atomicAdd(hi + o, v);
+    }
+}
+
+// Index of the source held in register slot q: vector loads give a thread
+// four consecutive sources per group, scalar loads one source per stride.
+__device__ __forceinline__ int src_index(int q, bool vec, int tid, int nt)
+{
+    return vec ? 4 * (tid + (q >> 2) * nt) + (q & 3) : tid + q * nt;
+}
+
+template <bool COMP, int MAXQ>
+__global__ void __launch_bounds__(512, 2) tau_scatter_kernel(const TauLaunch L)
+{
+    extern __shared__ __align__(16) float acc_smem[];
     const int N = L.n_pix;
     const int Wd = L.w_max;
     const int NE = N + 2 * Wd;
     const int tid = threadIdx.x, nt = blockDim.x;
-    Rec* rec = reinterpret_cast<Rec*>(smem_raw);
-    int* bin = reinterpret_cast<int*>(smem_raw + sizeof(Rec) * (size_t)N);   // N + 1
-    int* aux = bin + (N + 1);                                                 // N
-    int* reach = aux + N;                                                     // NE
-    short* Lb = reinterpret_cast<short*>(aux);
-    short* Rb = Lb + N;
+    float* hi = acc_smem;
+    float* lo = acc_smem + NE;
 
     const int64_t row = blockIdx.x;
     const int64_t sk = L.ids ? L.ids[row] : row;
@@ -286,139 +319,81 @@ __global__ void __launch_bounds__(512) tau_env_kernel(const TauLaunch L)
     const float* __restrict__ vpec = L.vpec + sk * (int64_t)N;
     const float* __restrict__ temp = L.temp ? L.temp + sk * (int64_t)N : nullptr;
 
-    // 1. inputs into registers (coalesced), histogram of target pixels
+    // 1. every input load issued up front (float4 when rows are 16-byte aligned),
+    //    accumulators cleared meanwhile
+    const bool vec = (N & 3) == 0;
     float r_[MAXQ], v_[MAXQ], T_[MAXQ];
-    int t_[MAXQ];
-    for (int k = tid; k <= N; k += nt) bin[k] = 0;
-    __syncthreads();
+    if (vec) {
 #pragma unroll
-    for (int q = 0; q < MAXQ; ++q) {
-        const int j = tid + q * nt;
-        r_[q] = 0.f;
-        if (j < N) {
-            r_[q] = rho[j];
-            v_[q] = vpec[j];
-            T_[q] = temp ? temp[j] : 0.f;
-            if (r_[q] > 0.f) {
-                if constexpr (PREC == LYA_PREC_F64)
-                    t_[q] = wrap_pixel((int64_t)j + (int64_t)rint((double)v_[q] * L.inv_du_d), N);
-                else
-                    t_[q] = wrap_pixel((int64_t)j + (int64_t)target_shift_f32(v_[q], L), N);
-                atomicAdd(&bin[t_[q] + 1], 1);
+        for (int g = 0; g < MAXQ / 4; ++g) {
+            const int grp = tid + g * nt;
+            if (4 * grp < N) {
+                const float4 a = __ldcs(reinterpret_cast<const float4*>(rho) + grp);
+                const float4 b = __ldcs(reinterpret_cast<const float4*>(vpec) + grp);
+                const float4 c = temp ? __ldcs(reinterpret_cast<const float4*>(temp) + grp)
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+                r_[4 * g] = a.x; r_[4 * g + 1] = a.y; r_[4 * g + 2] = a.z; r_[4 * g + 3] = a.w;
+                v_[4 * g] = b.x; v_[4 * g + 1] = b.y; v_[4 * g + 2] = b.z; v_[4 * g + 3] = b.w;
+                T_[4 * g] = c.x; T_[4 * g + 1] = c.y; T_[4 * g + 2] = c.z; T_[4 * g + 3] = c.w;
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) r_[4 * g + u] = 0.f;
             }
         }
+    } else {
+#pragma unroll
+        for (int q = 0; q < MAXQ; ++q) {
+            const int j = tid + q * nt;
+            r_[q] = j < N ? __ldcs(rho + j) : 0.f;
+            v_[q] = j < N ? __ldcs(vpec + j) : 0.f;
+            T_[q] = (j < N && temp) ? __ldcs(temp + j) : 0.f;
+        }
+    }
+    for (int e = tid; e < NE; e += nt) {
+        hi[e] = 0.f;
+        if constexpr (COMP) lo[e] = 0.f;
     }
     __syncthreads();
 
-    // 2. bin starts; scatter records {a, c r, w, j} and (target, half-width)
-    const int nsrc = block_exclusive_scan(bin + 1, N, warp_tot);
+    // 2. every source adds its line to the pixels within its reach
 #pragma unroll
     for (int q = 0; q < MAXQ; ++q) {
-        const int j = tid + q * nt;
+        const int j = src_index(q, vec, tid, nt);
         if (j >= N || !(r_[q] > 0.f)) continue;
-        int pos, t, h;
-        if constexpr (PREC == LYA_PREC_F64) {
-            const SrcF64 s = prep_f64(L, r_[q], v_[q], T_[q], j);
-            t = s.t; h = s.h;
-            pos = atomicAdd(&bin[t + 1], 1);
-            if (pos >= N) { atomicOr(L.err, 2); continue; }
-            rec[pos] = make_double4_32a(s.a, s.bb, s.w, (double)j);
-        } else {
-            const SrcF32 s = prep_f32(L, r_[q], v_[q], T_[q], j);
-            t = s.t; h = s.h;
-            pos = atomicAdd(&bin[t + 1], 1);
-            if (pos >= N) { atomicOr(L.err, 2); continue; }
-            rec[pos] = make_float4(s.a, s.bb, s.w, (float)j);
-        }
-        aux[pos] = (t << 16) | h;
-    }
-    for (int e = tid; e < NE; e += nt) reach[e] = kReachLow;
-    __syncthreads();
-
-    // 3. order inside each bin by source pixel j: rank by counting (parallel,
-    //    deterministic), then write back with the key replaced by the target
-    Rec rr[MAXQ];
-    int np[MAXQ], th[MAXQ];
-#pragma unroll
-    for (int q = 0; q < MAXQ; ++q) {
-        const int k = tid + q * nt;
-        np[q] = -1;
-        if (k < nsrc) {
-            rr[q] = rec[k];
-            th[q] = aux[k];
-            const int t = th[q] >> 16;
-            const int b0 = bin[t], b1 = bin[t + 1];
-            int rank = 0;
-            if (b1 - b0 > 1)
-                for (int k2 = b0; k2 < b1; ++k2) rank += rec[k2].w < rr[q].w;
-            np[q] = b0 + rank;
+        const SrcF32 s = prep_f32(L, r_[q], v_[q], T_[q], j);
+        float* const hi_t = hi + (s.t + Wd);
+        float* const lo_t = lo + (s.t + Wd);
+        float mf = (float)(-s.h);
+#pragma unroll 2
+        for (int m = -s.h; m <= s.h; ++m, mf += 1.f) {
+            const float x = fmaf(mf, s.a, -s.bb);
+            scatter_add<COMP>(hi_t, lo_t, m, s.w * ex2(-(x * x)));
         }
     }
     __syncthreads();
-#pragma unroll
-    for (int q = 0; q < MAXQ; ++q) {
-        if (np[q] < 0) continue;
-        const int t = th[q] >> 16, h = th[q] & 0xffff;
-        rr[q].w = (float)t;
-        rec[np[q]] = rr[q];
-        atomicMax(&reach[t + Wd], t + h);
-        if (t >= N - Wd) atomicMax(&reach[t - N + Wd], t - N + h);
-        if (t < Wd) atomicMax(&reach[t + N + Wd], t + N + h);
-    }
-    __syncthreads();
 
-    // 4. L_i from the prefix max of the right reach
-    block_prefix_max(reach, NE, warp_tot, kReachLow);
-    for (int i = tid; i < N; i += nt) Lb[i] = (short)(i + 1);
-    __syncthreads();
-    for (int e = tid; e < NE; e += nt) {
-        const int prev = e ? reach[e - 1] : kReachLow;
-        const int lo = max(prev + 1, 0), hi = min(reach[e], N - 1);
-        for (int i = lo; i <= hi; ++i) Lb[i] = (short)(e - Wd);
-    }
-    __syncthreads();
-    for (int e = tid; e < NE; e += nt) reach[e] = kReachHigh;
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < MAXQ; ++q) {
-        if (np[q] < 0) continue;
-        const int t = th[q] >> 16, h = th[q] & 0xffff;
-        atomicMin(&reach[t + Wd], t - h);
-        if (t >= N - Wd) atomicMin(&reach[t - N + Wd], t - N - h);
-        if (t < Wd) atomicMin(&reach[t + N + Wd], t + N - h);
-    }
-    __syncthreads();
-
-    // 5. R_i from the suffix min of the left reach
-    block_suffix_min(reach, NE, warp_tot, kReachHigh);
-    for (int i = tid; i < N; i += nt) Rb[i] = (short)(i - 1);
-    __syncthreads();
-    for (int e = tid; e < NE; e += nt) {
-        const int next = e + 1 < NE ? reach[e + 1] : kReachHigh;
-        const int lo = max(reach[e], 0), hi = min(next - 1, N - 1);
-        for (int i = lo; i <= hi; ++i) Rb[i] = (short)(e - Wd);
-    }
-    __syncthreads();
-
-    // 6. pair sums over [L_i, R_i], split where the run crosses the periodic seam
+    // 3. fold the halo back across the periodic seam and write tau
+    const float K = L.K;
     for (int i = tid; i < N; i += nt) {
-        Acc acc;
-        const float fi = (float)i;
-        const int lx = Lb[i], rx = Rb[i];
-        if (lx <= rx) {
-            if (lx < 0) {
-                const int u1 = min(rx, -1);
-                pair_segment<PREC>(rec, bin[lx + N], bin[u1 + N + 1], fi + (float)N, acc);
+        float s = hi[i + Wd];
+        if constexpr (COMP) {
+            float err = lo[i + Wd];
+            if (i < Wd) {
+                const float x = hi[i + Wd + N], t = __fadd_rn(s, x);
+                err = __fadd_rn(err, __fadd_rn(two_sum_err(s, x, t), lo[i + Wd + N]));
+                s = t;
             }
-            const int a0 = max(lx, 0), a1 = min(rx, N - 1);
-            if (a0 <= a1) pair_segment<PREC>(rec, bin[a0], bin[a1 + 1], fi, acc);
-            if (rx >= N) {
-                const int u0 = max(lx, N) - N;
-                pair_segment<PREC>(rec, bin[u0], bin[rx - N + 1], fi - (float)N, acc);
+            if (i >= N - Wd) {
+                const float x = hi[i + Wd - N], t = __fadd_rn(s, x);
+                err = __fadd_rn(err, __fadd_rn(two_sum_err(s, x, t), lo[i + Wd - N]));
+                s = t;
             }
+            out[i] = K * __fadd_rn(s, err);
+        } else {
+            if (i < Wd) s = __fadd_rn(s, hi[i + Wd + N]);
+            if (i >= N - Wd) s = __fadd_rn(s, hi[i + Wd - N]);
+            out[i] = K * s;
         }
-        if constexpr (PREC == LYA_PREC_F64) out[i] = (float)(L.K_d * Prec<PREC>::value(acc));
-        else out[i] = L.K * Prec<PREC>::value(acc);
     }
 }
 
@@ -431,33 +406,22 @@ int block_threads(int n_pix)
 
 }  // namespace
 
-static size_t rec_bytes(int precision)
+// FP64 comparator (whole-skewer-window gather): records | bin starts.
+static size_t global_smem_bytes(int n_pix)
 {
-    return precision == LYA_PREC_F64 ? sizeof(double4_32a) : sizeof(float4);
+    return sizeof(double4_32a) * (size_t)n_pix + sizeof(int) * (size_t)(n_pix + 1);
 }
 
-// Adaptive-window layout: records, bin starts, aux, reach.
-static size_t env_smem_bytes(int n_pix, int w_max, int precision)
+// FP32 scatter: hi (and lo when compensated) accumulators with halos.
+static size_t scatter_smem_bytes(int n_pix, int w_max, bool comp)
 {
-    return rec_bytes(precision) * (size_t)n_pix + sizeof(int) * (size_t)(n_pix + 1) +
-           sizeof(int) * (size_t)n_pix + sizeof(int) * (size_t)(n_pix + 2 * w_max);
-}
-
-// Whole-skewer-window layout: records, bin starts.
-static size_t global_smem_bytes(int n_pix, int precision)
-{
-    return rec_bytes(precision) * (size_t)n_pix + sizeof(int) * (size_t)(n_pix + 1);
-}
-
-static bool use_env(int n_pix, int w_max, int precision)
-{
-    return n_pix <= 4096 && env_smem_bytes(n_pix, w_max, precision) <= max_dynamic_smem();
+    return (comp ? 2 : 1) * sizeof(float) * (size_t)(n_pix + 2 * w_max);
 }
 
 size_t tau_smem_bytes(int n_pix, int w_max, int precision)
 {
-    return use_env(n_pix, w_max, precision) ? env_smem_bytes(n_pix, w_max, precision)
-                                            : global_smem_bytes(n_pix, precision);
+    if (precision == LYA_PREC_F64) return global_smem_bytes(n_pix);
+    return scatter_smem_bytes(n_pix, w_max, precision == LYA_PREC_F32_COMPENSATED);
 }
 
 template <typename K>
@@ -473,23 +437,24 @@ static cudaError_t launch_kernel(K kernel, const TauLaunch& L, size_t smem, cuda
     return cudaGetLastError();
 }
 
-template <int PREC>
-static cudaError_t launch_prec(const TauLaunch& L, cudaStream_t stream)
+template <bool COMP>
+static cudaError_t launch_scatter(const TauLaunch& L, cudaStream_t stream)
 {
-    if (!use_env(L.n_pix, L.w_max, PREC))
-        return launch_kernel(tau_kernel<PREC>, L, global_smem_bytes(L.n_pix, PREC), stream);
-    const size_t smem = env_smem_bytes(L.n_pix, L.w_max, PREC);
-    const int q = (L.n_pix + block_threads(L.n_pix) - 1) / block_threads(L.n_pix);
-    if (q <= 4) return launch_kernel(tau_env_kernel<PREC, 4>, L, smem, stream);
-    return launch_kernel(tau_env_kernel<PREC, 8>, L, smem, stream);
+    const size_t smem = scatter_smem_bytes(L.n_pix, L.w_max, COMP);
+    const int nt = block_threads(L.n_pix);
+    const int q = (L.n_pix + nt - 1) / nt;
+    if (q <= 4) return launch_kernel(tau_scatter_kernel<COMP, 4>, L, smem, stream);
+    if (q <= 8) return launch_kernel(tau_scatter_kernel<COMP, 8>, L, smem, stream);
+    return launch_kernel(tau_scatter_kernel<COMP, 16>, L, smem, stream);
 }
 
 cudaError_t launch_tau(const TauLaunch& L, int precision, cudaStream_t stream)
 {
     switch (precision) {
-    case LYA_PREC_F32_COMPENSATED: return launch_prec<LYA_PREC_F32_COMPENSATED>(L, stream);
-    case LYA_PREC_F32_NAIVE: return launch_prec<LYA_PREC_F32_NAIVE>(L, stream);
-    case LYA_PREC_F64: return launch_prec<LYA_PREC_F64>(L, stream);
+    case LYA_PREC_F32_COMPENSATED: return launch_scatter<true>(L, stream);
+    case LYA_PREC_F32_NAIVE: return launch_scatter<false>(L, stream);
+    case LYA_PREC_F64:
+        return launch_kernel(tau_kernel<LYA_PREC_F64>, L, global_smem_bytes(L.n_pix), stream);
     default: return cudaErrorInvalidValue;
     }
 }

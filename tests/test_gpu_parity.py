@@ -102,16 +102,23 @@ def test_power_law_temperature(lya, orc, pivot, gamma):
     assert float(np.abs(F_g - F_o).max()) <= F_ATOL
 
 
-def test_deterministic(lya):
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_repeat_runs_agree(lya, precision):
+    """Atomic adds land in any order: repeated runs agree to the accumulation's
+    rounding (the compensated sum to ~1 ulp), the FP64 gather bit for bit."""
     import torch
     spec = ls.TINY_20MPC
     rho, v, t = ls.skewers(spec, np.arange(32))
     field = make_field(lya, spec, rho, v, t)
-    p = lya.ExtractParams()
+    p = lya.ExtractParams(precision=precision)
     a = lya.extract_skewers(field, p)
     b = lya.extract_skewers(field, p)
     torch.cuda.synchronize()
-    assert torch.equal(a, b)
+    if precision == 2:
+        assert torch.equal(a, b)
+    else:
+        rel = ((a - b).abs() / a.abs().clamp_min(1e-30)).max().item()
+        assert rel <= (3e-7 if precision == 0 else 1e-5)
 
 
 # ----------------------------------------------------------------------------
@@ -161,11 +168,13 @@ def test_ids_subset_duplicates_and_errors(lya):
     full = lya.extract_skewers(field, p)
     sub = lya.extract_skewers(field, p, ids=[5, 1, 5])
     torch.cuda.synchronize()
-    assert torch.equal(sub[0], full[5]) and torch.equal(sub[1], full[1]) and torch.equal(sub[2], full[5])
+    for r, sk in enumerate([5, 1, 5]):        # equal up to the order atomic adds landed in
+        torch.testing.assert_close(sub[r], full[sk], rtol=1e-6, atol=0)
     field.status()                                   # no error so far
     bad = lya.extract_skewers(field, p, ids=[2, 99])
     torch.cuda.synchronize()
-    assert torch.equal(bad[0], full[2]) and bool((bad[1] == 0).all())
+    torch.testing.assert_close(bad[0], full[2], rtol=1e-6, atol=0)
+    assert bool((bad[1] == 0).all())
     with pytest.raises(lya.LyaError):
         field.status()
     field.status()                                   # cleared
