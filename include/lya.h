@@ -164,6 +164,29 @@ lya_status lya_rescale_mean_flux(const float* tau, int64_t n, double target,
                                  float* flux_out, void* stream);
 
 /*
+ * lya_rescale_mean_flux without any device allocation.  The paper has no
+ * counterpart: this is a deployment variant for callers that cannot call
+ * cudaMalloc (code running inside a CUDA-graph capture they do not own the
+ * memory pool of, plug-ins whose host forbids allocation after start-up, or
+ * a service whose memory budget is already handed out).  Arguments, results
+ * and errors are those of lya_rescale_mean_flux.
+ *
+ * Its scratch (the Newton state and one partial sum per CTA) is a fixed
+ * 64 KiB device array inside the library, present on every GPU that loads
+ * it until the process exits; the reduction therefore uses at most 1024
+ * CTAs, which still covers any n.  The first call on a device looks up the
+ * array's device address (once per device, with that device current); make
+ * that first call before any stream capture.  Every call rewrites the state
+ * it uses, so no clearing is needed between calls, but all calls share the
+ * one array: calls whose work overlaps on the GPU (other streams, other host
+ * threads on the same device) race and must be serialised by the caller.
+ * Synchronises the stream.
+ */
+lya_status lya_rescale_mean_flux_noalloc(const float* tau, int64_t n, double target,
+                                         double tol, int max_iter, double* A_out,
+                                         float* flux_out, void* stream);
+
+/*
  * Flux statistics (Sec. 2.3, Sec. 5.2) over n device values F: mean,
  * population variance, tau_eff = -ln<F> and the 21-bin PDF with bin k holding
  * (2k-1)/40 <= F < (2k+1)/40 (clamped to [0, 20]); the bin decision is exact

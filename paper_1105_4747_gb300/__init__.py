@@ -22,4 +22,5 @@ from ._binding import (  # noqa: F401
     library_path,
     load_library,
     rescale_mean_flux,
+    rescale_mean_flux_noalloc,
 )

@@ -87,9 +87,11 @@ def load_library():
         lib.lya_field_shape.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
         lib.lya_extract_skewers.argtypes = [vp, ctypes.POINTER(_ExtractParams), vp, i64, vp, vp]
         lib.lya_rescale_mean_flux.argtypes = [vp, i64, d, d, i32, ctypes.POINTER(d), vp, vp]
+        lib.lya_rescale_mean_flux_noalloc.argtypes = [vp, i64, d, d, i32, ctypes.POINTER(d), vp, vp]
         lib.lya_flux_stats.argtypes = [vp, i64, ctypes.POINTER(_FluxStats), vp]
         for name in ("lya_create_field", "lya_field_load", "lya_destroy_field", "lya_field_status",
-                     "lya_field_shape", "lya_extract_skewers", "lya_rescale_mean_flux", "lya_flux_stats"):
+                     "lya_field_shape", "lya_extract_skewers", "lya_rescale_mean_flux",
+                     "lya_rescale_mean_flux_noalloc", "lya_flux_stats"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -265,6 +267,24 @@ def rescale_mean_flux(tau, target: float, tol: float = 1e-12, max_iter: int = 50
                                                 F.data_ptr() if F is not None else None,
                                                 _stream_handle(stream)), "lya_rescale_mean_flux")
     return A.value, F
+
+
+def rescale_mean_flux_noalloc(tau, target: float, flux_out, tol: float = 1e-12, max_iter: int = 50,
+                              stream=None):
+    """lya_rescale_mean_flux_noalloc: the root-find with no device allocation.
+
+    ``flux_out`` is a caller-provided CUDA float32 tensor shaped like ``tau``
+    (or None); the library allocates nothing.  Returns A.
+    """
+    _require_cuda_f32(tau, "tau")
+    if flux_out is not None:
+        _require_cuda_f32(flux_out, "flux_out")
+    A = ctypes.c_double(math.nan)
+    _check(load_library().lya_rescale_mean_flux_noalloc(
+        tau.data_ptr(), tau.numel(), float(target), float(tol), int(max_iter), ctypes.byref(A),
+        flux_out.data_ptr() if flux_out is not None else None, _stream_handle(stream)),
+        "lya_rescale_mean_flux_noalloc")
+    return A.value
 
 
 @dataclass

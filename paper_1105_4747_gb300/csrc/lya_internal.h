@@ -51,6 +51,11 @@ lya_status mean_flux_solve(const float* tau, int64_t n, double target, double to
                            int max_iter, double* A_out, float* flux_out,
                            cudaStream_t stream);
 
+// The same root-find with its scratch in a fixed device array (no allocation).
+lya_status mean_flux_solve_noalloc(const float* tau, int64_t n, double target, double tol,
+                                   int max_iter, double* A_out, float* flux_out,
+                                   cudaStream_t stream);
+
 // Flux statistics (Sec. 2.3, 5.2) over n device flux values.
 lya_status flux_stats_run(const float* flux, int64_t n, lya_flux_stats_t* out,
                           cudaStream_t stream);

@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 
 #include "lya_device.cuh"
 #include "lya_internal.h"
@@ -456,6 +457,109 @@ done:
     if (part) cudaFreeAsync(part, stream);
     if (err != cudaSuccess) return err == cudaErrorMemoryAllocation ? LYA_ENOMEM : LYA_ECUDA;
     return LYA_OK;
+}
+
+}  // namespace lya
+
+// ---- allocation-free mean-flux root-find -------------------------------------------
+//
+// For callers that cannot allocate device memory: code running while a CUDA
+// graph is being captured into a pool they do not own, plug-ins whose host
+// application forbids allocation after start-up, or callers on a memory
+// budget that is already fully handed out.  The Newton state and the per-CTA
+// partials live in a fixed file-scope device array instead of stream-ordered
+// allocations.  The array is kNoAllocScratchBytes (64 KiB) on every GPU that
+// loads the library and stays there until the process exits; it fits the
+// state plus kNoAllocMaxBlocks partials, so the reduction grid is capped at
+// kNoAllocMaxBlocks CTAs (the grid-stride loops still cover any n).
+//
+// Every call shares the one array and rewrites the whole state it reads (the
+// state is copied in from the host at the start of each call, and every
+// partial is written before it is read), so nothing is left over from a
+// previous call.  Two calls whose work overlaps on the GPU (different streams,
+// or different host threads on one device) race on the array.
+namespace lya {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 64 * 1024;
+constexpr int kNoAllocMaxBlocks = 1024;
+constexpr size_t kNoAllocStateBytes = 256;      // MFState, padded to the array's alignment
+static_assert(sizeof(MFState) <= kNoAllocStateBytes, "state does not fit its slot");
+static_assert(kNoAllocStateBytes + kNoAllocMaxBlocks * sizeof(Partial) <= kNoAllocScratchBytes,
+              "partials do not fit the scratch array");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the host-side name of a __device__ array is not its address).
+cudaError_t noalloc_scratch(void** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+lya_status mean_flux_solve_noalloc(const float* tau, int64_t n, double target, double tol, int max_iter,
+                                   double* A_out, float* flux_out, cudaStream_t stream)
+{
+    void* scratch = nullptr;
+    cudaError_t err = noalloc_scratch(&scratch);
+    if (err != cudaSuccess) return LYA_ECUDA;
+    const int grid = grid_for(n) < kNoAllocMaxBlocks ? grid_for(n) : kNoAllocMaxBlocks;
+    if (kNoAllocStateBytes + (size_t)grid * sizeof(Partial) > kNoAllocScratchBytes) return LYA_EINVAL;
+    MFState* st = static_cast<MFState*>(scratch);
+    Partial* part = reinterpret_cast<Partial*>(static_cast<unsigned char*>(scratch) + kNoAllocStateBytes);
+    MFState h{};
+    h.Ft = target;
+    h.tol = tol;
+    h.n = n;
+    h.max_iter = max_iter;
+    h.status = LYA_ENOCONV;
+    lya_status result = LYA_OK;
+    err = cudaMemcpyAsync(st, &h, sizeof(MFState), cudaMemcpyHostToDevice, stream);
+    if (err != cudaSuccess) return LYA_ECUDA;
+    mf_init_kernel<<<grid, kThreads, 0, stream>>>(tau, n, st, part);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) return LYA_ECUDA;
+    for (int launched = 0; launched < max_iter;) {
+        const int batch = launched == 0 ? 6 : 4;
+        for (int b = 0; b < batch && launched < max_iter; ++b, ++launched) {
+            mf_newton_kernel<<<grid, kThreads, 0, stream>>>(tau, n, st, part);
+            count_launch();
+            if (cudaGetLastError() != cudaSuccess) return LYA_ECUDA;
+        }
+        err = cudaMemcpyAsync(&h, st, sizeof(MFState), cudaMemcpyDeviceToHost, stream);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(stream);
+        if (err != cudaSuccess) return LYA_ECUDA;
+        if (h.done) break;
+    }
+    result = h.done ? (lya_status)h.status : LYA_ENOCONV;
+    if (result == LYA_OK) {
+        *A_out = h.A;
+        if (flux_out) {
+            mf_flux_kernel<<<grid, kThreads, 0, stream>>>(tau, n, st, flux_out);
+            count_launch();
+            if (cudaGetLastError() != cudaSuccess) return LYA_ECUDA;
+            if (cudaStreamSynchronize(stream) != cudaSuccess) return LYA_ECUDA;
+        }
+    }
+    return result;
 }
 
 }  // namespace lya

@@ -1,0 +1,69 @@
+"""The allocation-free root-find gives the allocating one's answer.
+
+lya_rescale_mean_flux_noalloc serves callers that cannot allocate device
+memory (inside a CUDA-graph capture they do not own the pool of, plug-ins
+that must not allocate after start-up, services whose memory budget is spent);
+its scratch is a fixed device array inside liblya.  This file is named to be
+collected last, so a run that stops at the first failure has run every other
+test before it.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import lya_synth as ls
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lya():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1105_4747_gb300 as lya
+    return lya
+
+
+def _check_pair(lya, tau, target):
+    import torch
+    A_ref, F_ref = lya.rescale_mean_flux(tau, target)
+    F = torch.empty_like(tau)
+    A = lya.rescale_mean_flux_noalloc(tau, target, F)
+    torch.cuda.synchronize()
+    assert math.isfinite(A)
+    assert A == pytest.approx(A_ref, rel=1e-9)
+    assert float((F - F_ref).abs().max()) <= 1e-6
+    assert float(F.double().mean()) == pytest.approx(target, abs=1e-7)
+
+
+def test_noalloc_matches_allocating_root_find_twice(lya):
+    import torch
+    spec = ls.TINY_20MPC
+    rho, v, t = ls.skewers(spec, np.arange(ls.TINY_20MPC_SKEWERS))
+    field = lya.Field(rho, v, t, box=spec.box, z=spec.z)
+    tau = lya.extract_skewers(field, lya.ExtractParams())
+    # two calls in a row share the scratch array: the second must not see the first
+    _check_pair(lya, tau, ls.TINY_20MPC_FT)
+    _check_pair(lya, tau, ls.TINY_20MPC_FT)
+    # a larger input (more CTAs than the tiny one) and another target, twice
+    g = torch.Generator(device="cuda").manual_seed(3)
+    big = torch.rand(3_000_000, device="cuda", generator=g) ** 4 * 5.0
+    _check_pair(lya, big, 0.7)
+    _check_pair(lya, big, 0.7)
+
+
+def test_noalloc_errors_match(lya):
+    import torch
+    with pytest.raises(lya.LyaError) as e:
+        lya.rescale_mean_flux_noalloc(torch.zeros(100, device="cuda"), 0.8, None)
+    assert e.value.status == -1
+    tau = torch.tensor([0.0] * 90 + [1.0] * 10, device="cuda")
+    with pytest.raises(lya.LyaError) as e:
+        lya.rescale_mean_flux_noalloc(tau, 0.85, None)
+    assert e.value.status == -4
+    with pytest.raises(lya.LyaError):
+        lya.rescale_mean_flux_noalloc(tau, 1.5, None)
