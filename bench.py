@@ -304,7 +304,7 @@ def run_ours(args):
     achieved = ALG_BYTES_PER_PX * n_px / (tau_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None,
-                "kernel": "tau_scatter_kernel<compensated,8>", "kernel_ms": tau_ms,
+                "kernel": "tau_tile_kernel<compensated,8>", "kernel_ms": tau_ms,
                 "peak_source": "measured" if peaks else "fallback",
                 "alg_bytes_per_launch": ALG_BYTES_PER_PX * n_px}
 

@@ -1,9 +1,10 @@
 // tau_extract.cu -- optical depth along skewers (Eq. 4-6), sm_103a.
 //
 // One CTA owns one skewer.  Two kernels:
-//   * tau_scatter_kernel (FP32, the product path): every source adds its
-//     thermally broadened line to the pixels within nsigma Doppler widths
-//     of its target, accumulating in shared memory (compensated or plain);
+//   * tau_tile_kernel (FP32, the product path): sources counting-sorted by
+//     target pixel; lane pairs own four-pixel tiles, taken in order of
+//     candidate count, and sum the sources whose reach covers the tile
+//     (compensated or plain);
 //   * tau_kernel (FP64 comparator): sources counting-sorted by target pixel,
 //     then each output pixel sums the sources of the bins within the
 //     skewer's widest reach.
@@ -244,50 +245,39 @@ __global__ void __launch_bounds__(512) tau_kernel(const TauLaunch L)
     }
 }
 
-// ---- scatter kernel (FP32) --------------------------------------------------------
+// ---- tile kernel (FP32) -----------------------------------------------------------
 //
-// One CTA owns one skewer and keeps its optical depth in shared memory.
-// Every source j adds its line, w_j 2^-(c_j (m du - r_j))^2, to the pixels
-// t_j + m, |m| <= h_j, where h_j = floor((nsigma b_j + |r_j|)/du) is the
-// exact reach of the nsigma b_j cut: the work is one MUFU ex2 and one
-// shared-memory atomic add per kept pair, with no sort and no window search.
+// Sources are counting-sorted by target pixel into shared memory.  Source j
+// covers the pixels |i - t_j| <= h_j, h_j = floor((nsigma b_j + |r_j|)/du).
+// The output pixels are cut into tiles of kTile consecutive pixels; a tile's
+// candidate sources are the sorted run of target bins [L, R] with
+//   L = first bin t with max_{t' <= t}(t' + h_t') >= first pixel of the tile
+//   R = last  bin t with min_{t' >= t}(t' - h_t') <= last pixel of the tile
+// (prefix max of the right reach, suffix min of the left reach, over bins
+// extended by w_max on both sides so the periodic wrap is explicit).  This
+// holds every source covering the tile and, away from the broadest lines,
+// little else.
 //
-// The accumulator is extended by w_max pixels on each side, so a line that
-// crosses the periodic seam lands in a halo slot; the halo is folded back
-// onto the skewer before the write-out.
+// Load balance: the tiles are counting-sorted by candidate count, largest
+// first, and handed to lane pairs in that order, so the sixteen pairs of a
+// warp walk lists of nearly equal length.  Each lane owns two adjacent pixels
+// of its tile: a candidate record is read once from shared memory and
+// evaluated for both (one MUFU ex2 each).  tau is gathered in shared memory
+// and written to HBM in order at the end.
 //
-// Compensated variant: the add is an atomic that returns the old value, so
-// the thread knows exactly which FP32 addition the memory performed and
-// recovers its rounding error with TwoSum (old + v = s + e exactly); the
-// errors e go to a second array by plain atomic adds.  hi + lo equals the
-// exact sum of the terms up to O(n u^2), whatever order the atomics ran in.
-// Naive variant: one plain atomic add per pair.  In both, the order in which
-// atomics from different threads land is not fixed, so repeated runs agree
-// to the accumulation's rounding (the compensated one to ~1 ulp of tau), not
-// bit for bit.
+// Accumulation per pixel: the terms of four consecutive candidates are added
+// plainly, then folded into a Kahan sum (compensated variant); or every term
+// is added plainly (naive variant).
 //
-// Shared memory: hi (N + 2 w_max floats) | lo (N + 2 w_max floats, compensated only).
+// Shared memory: records (N rounded up to 4) | bin starts (N+1, padded to 4) |
+// reach (N + 2 w_max; later tau) | tile runs L, R and the tile order (int16).
+constexpr int kTile = 4;
+constexpr int kLanesPerTile = 2;                 // each lane: kTile / kLanesPerTile pixels
+constexpr int kTileKeys = 256;                   // tile-order histogram (counts >= 255 share a key)
+constexpr int kReachLow = -(1 << 28);
+constexpr int kReachHigh = 1 << 28;
 
-// Exact rounding error of s = fl(a + b): a + b = s + e (Knuth's TwoSum).
-__device__ __forceinline__ float two_sum_err(float a, float b, float s)
-{
-    const float bp = __fsub_rn(s, a);
-    const float ap = __fsub_rn(s, bp);
-    return __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
-}
-
-template <bool COMP>
-__device__ __forceinline__ void scatter_add(float* hi, float* lo, int o, float v)
-{
-    if constexpr (COMP) {
-        const float old = atomicAdd(hi + o, v);
-        const float s = __fadd_rn(old, v);
-        const float e = two_sum_err(old, v, s);
-        if (e != 0.f) atomicAdd(lo + o, e);
-    } else {
-        atomicAdd(hi + o, v);
-    }
-}
+__host__ __device__ __forceinline__ int round_up4(int n) { return (n + 3) & ~3; }
 
 // Index of the source held in register slot q: vector loads give a thread
 // four consecutive sources per group, scalar loads one source per stride.
@@ -296,16 +286,76 @@ __device__ __forceinline__ int src_index(int q, bool vec, int tid, int nt)
     return vec ? 4 * (tid + (q >> 2) * nt) + (q & 3) : tid + q * nt;
 }
 
-template <bool COMP, int MAXQ>
-__global__ void __launch_bounds__(512, 2) tau_scatter_kernel(const TauLaunch L)
+// The sorted-source pieces of extended bins [lx, rx], split where the run
+// crosses the periodic seam: f(k0, k1, shift) for up to three pieces with
+// frame shifts +N, 0, -N.
+template <typename F>
+__device__ __forceinline__ void for_tile_run(const int* bin, int N, int lx, int rx, F&& f)
 {
-    extern __shared__ __align__(16) float acc_smem[];
+    if (lx > rx) return;
+    if (lx < 0) f(bin[lx + N], bin[min(rx, -1) + N + 1], (float)N);
+    const int a0 = max(lx, 0), a1 = min(rx, N - 1);
+    if (a0 <= a1) f(bin[a0], bin[a1 + 1], 0.f);
+    if (rx >= N) f(bin[max(lx, N) - N], bin[rx - N + 1], -(float)N);
+}
+
+// Two adjacent pixels fo, fo + 1 (in the run's frame) against candidates [k0, k1).
+template <bool COMP>
+__device__ __forceinline__ void pair2_segment(const float4* __restrict__ rec, int k0, int k1, float fo,
+                                              float (&S)[2], float (&C)[2])
+{
+    int k = k0;
+    if constexpr (COMP) {
+        for (; k < k1;) {
+            float P0 = 0.f, P1 = 0.f;
+            const int kk = min(k + 4, k1);
+            for (; k < kk; ++k) {
+                const float4 r = rec[k];                     // {a, c r, w, t}
+                const float x0 = fmaf(fo - r.w, r.x, -r.y);
+                const float x1 = x0 + r.x;
+                P0 = fmaf(r.z, ex2(-(x0 * x0)), P0);
+                P1 = fmaf(r.z, ex2(-(x1 * x1)), P1);
+            }
+            float y = __fsub_rn(P0, C[0]);                   // Kahan folds of the block sums
+            float t = __fadd_rn(S[0], y);
+            C[0] = __fsub_rn(__fsub_rn(t, S[0]), y);
+            S[0] = t;
+            y = __fsub_rn(P1, C[1]);
+            t = __fadd_rn(S[1], y);
+            C[1] = __fsub_rn(__fsub_rn(t, S[1]), y);
+            S[1] = t;
+        }
+    } else {
+#pragma unroll 2
+        for (; k < k1; ++k) {
+            const float4 r = rec[k];
+            const float x0 = fmaf(fo - r.w, r.x, -r.y);
+            const float x1 = x0 + r.x;
+            S[0] = fmaf(r.z, ex2(-(x0 * x0)), S[0]);
+            S[1] = fmaf(r.z, ex2(-(x1 * x1)), S[1]);
+        }
+    }
+}
+
+template <bool COMP, int MAXQ>
+__global__ void __launch_bounds__(512, MAXQ <= 8 ? 2 : 1) tau_tile_kernel(const TauLaunch L)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int warp_tot[33];
+    __shared__ int tile_hist[kTileKeys];
+
     const int N = L.n_pix;
     const int Wd = L.w_max;
     const int NE = N + 2 * Wd;
+    const int NT = (N + kTile - 1) / kTile;
     const int tid = threadIdx.x, nt = blockDim.x;
-    float* hi = acc_smem;
-    float* lo = acc_smem + NE;
+    float4* rec = reinterpret_cast<float4*>(smem_raw);
+    int* bin = reinterpret_cast<int*>(rec + round_up4(N));   // N + 1 (padded to 4)
+    int* reach = bin + round_up4(N + 1);                     // NE; tau once the runs are known
+    float* tau_s = reinterpret_cast<float*>(reach);
+    short* Lt = reinterpret_cast<short*>(reach + NE);        // NT
+    short* Rt = Lt + NT;                                     // NT
+    short* order = Rt + NT;                                  // NT: tiles by candidate count
 
     const int64_t row = blockIdx.x;
     const int64_t sk = L.ids ? L.ids[row] : row;
@@ -319,8 +369,7 @@ __global__ void __launch_bounds__(512, 2) tau_scatter_kernel(const TauLaunch L)
     const float* __restrict__ vpec = L.vpec + sk * (int64_t)N;
     const float* __restrict__ temp = L.temp ? L.temp + sk * (int64_t)N : nullptr;
 
-    // 1. every input load issued up front (float4 when rows are 16-byte aligned),
-    //    accumulators cleared meanwhile
+    // 1. every input load issued up front (float4 when rows are 16-byte aligned)
     const bool vec = (N & 3) == 0;
     float r_[MAXQ], v_[MAXQ], T_[MAXQ];
     if (vec) {
@@ -349,51 +398,126 @@ __global__ void __launch_bounds__(512, 2) tau_scatter_kernel(const TauLaunch L)
             T_[q] = (j < N && temp) ? __ldcs(temp + j) : 0.f;
         }
     }
-    for (int e = tid; e < NE; e += nt) {
-        hi[e] = 0.f;
-        if constexpr (COMP) lo[e] = 0.f;
-    }
+    for (int k = tid; k <= N; k += nt) bin[k] = 0;
+    for (int e = tid; e < NE; e += nt) reach[e] = kReachLow;
+    for (int k = tid; k < kTileKeys; k += nt) tile_hist[k] = 0;
     __syncthreads();
 
-    // 2. every source adds its line to the pixels within its reach
+    // 2. per-source constants (kept in registers) and the histogram of target
+    //    pixels; th_ packs (target << 16) | reach, -1 = no source
+    float a_[MAXQ], bb_[MAXQ], w_[MAXQ];
+    int th_[MAXQ];
 #pragma unroll
     for (int q = 0; q < MAXQ; ++q) {
         const int j = src_index(q, vec, tid, nt);
-        if (j >= N || !(r_[q] > 0.f)) continue;
-        const SrcF32 s = prep_f32(L, r_[q], v_[q], T_[q], j);
-        float* const hi_t = hi + (s.t + Wd);
-        float* const lo_t = lo + (s.t + Wd);
-        float mf = (float)(-s.h);
-#pragma unroll 2
-        for (int m = -s.h; m <= s.h; ++m, mf += 1.f) {
-            const float x = fmaf(mf, s.a, -s.bb);
-            scatter_add<COMP>(hi_t, lo_t, m, s.w * ex2(-(x * x)));
+        th_[q] = -1;
+        if (j < N && r_[q] > 0.f) {
+            const SrcF32 s = prep_f32(L, r_[q], v_[q], T_[q], j);
+            a_[q] = s.a;
+            bb_[q] = s.bb;
+            w_[q] = s.w;
+            th_[q] = (s.t << 16) | s.h;
+            atomicAdd(&bin[s.t + 1], 1);
         }
     }
     __syncthreads();
 
-    // 3. fold the halo back across the periodic seam and write tau
-    const float K = L.K;
-    for (int i = tid; i < N; i += nt) {
-        float s = hi[i + Wd];
-        if constexpr (COMP) {
-            float err = lo[i + Wd];
-            if (i < Wd) {
-                const float x = hi[i + Wd + N], t = __fadd_rn(s, x);
-                err = __fadd_rn(err, __fadd_rn(two_sum_err(s, x, t), lo[i + Wd + N]));
-                s = t;
-            }
-            if (i >= N - Wd) {
-                const float x = hi[i + Wd - N], t = __fadd_rn(s, x);
-                err = __fadd_rn(err, __fadd_rn(two_sum_err(s, x, t), lo[i + Wd - N]));
-                s = t;
-            }
-            out[i] = K * __fadd_rn(s, err);
-        } else {
-            if (i < Wd) s = __fadd_rn(s, hi[i + Wd + N]);
-            if (i >= N - Wd) s = __fadd_rn(s, hi[i + Wd - N]);
-            out[i] = K * s;
+    // 3. bin starts; scatter the records {a, c r, w, t} and every source's
+    //    right reach t + h (three periodic images)
+    block_exclusive_scan(bin + 1, N, warp_tot);
+#pragma unroll
+    for (int q = 0; q < MAXQ; ++q) {
+        if (th_[q] < 0) continue;
+        const int t = th_[q] >> 16, h = th_[q] & 0xffff;
+        const int pos = atomicAdd(&bin[t + 1], 1);
+        if (pos >= N) { atomicOr(L.err, 2); th_[q] = -1; continue; }   // input changed under the kernel
+        rec[pos] = make_float4(a_[q], bb_[q], w_[q], (float)t);
+        atomicMax(&reach[t + Wd], t + h);
+        if (t >= N - Wd) atomicMax(&reach[t - N + Wd], t - N + h);
+        if (t < Wd) atomicMax(&reach[t + N + Wd], t + N + h);
+    }
+    __syncthreads();
+
+    // 4. first candidate bin of every tile, from the prefix max of the right reach
+    block_prefix_max(reach, NE, warp_tot, kReachLow);          // ends with a barrier
+    for (int tile = tid; tile < NT; tile += nt) Lt[tile] = (short)(kTile * tile + 1);   // no source reaches it
+    __syncthreads();
+    for (int e = tid; e < NE; e += nt) {
+        const int prev = e ? reach[e - 1] : kReachLow;
+        const int hi = min(reach[e], N - 1);
+        if (hi < 0) continue;
+        for (int tile = max((max(prev, -4) + 1 + kTile - 1) / kTile, 0); tile * kTile <= hi; ++tile)
+            Lt[tile] = (short)(e - Wd);
+    }
+    __syncthreads();
+    for (int e = tid; e < NE; e += nt) reach[e] = kReachHigh;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < MAXQ; ++q) {
+        if (th_[q] < 0) continue;
+        const int t = th_[q] >> 16, h = th_[q] & 0xffff;
+        atomicMin(&reach[t + Wd], t - h);
+        if (t >= N - Wd) atomicMin(&reach[t - N + Wd], t - N - h);
+        if (t < Wd) atomicMin(&reach[t + N + Wd], t + N - h);
+    }
+    __syncthreads();
+
+    // 5. last candidate bin of every tile, from the suffix min of the left reach
+    block_suffix_min(reach, NE, warp_tot, kReachHigh);         // ends with a barrier
+    for (int tile = tid; tile < NT; tile += nt) Rt[tile] = (short)(min(kTile * tile + kTile - 1, N - 1) - 1);
+    __syncthreads();
+    for (int e = tid; e < NE; e += nt) {
+        const int next = e + 1 < NE ? reach[e + 1] : kReachHigh;
+        const int lo = max(reach[e], 0), hi = min(next - 1, N - 1);
+        if (lo > hi) continue;
+        const int last = hi == N - 1 ? NT - 1 : (hi - (kTile - 1)) / kTile - (hi < kTile - 1);
+        for (int tile = lo / kTile; tile <= last; ++tile) Rt[tile] = (short)(e - Wd);
+    }
+    __syncthreads();
+
+    // 6. tiles ordered by candidate count, largest first (counting sort)
+    constexpr int kMaxTilesPerThread = (8192 / kTile + 255) / 256;
+    int tkey[kMaxTilesPerThread];
+#pragma unroll
+    for (int u = 0; u < kMaxTilesPerThread; ++u) {
+        const int tile = tid + u * nt;
+        tkey[u] = -1;
+        if (tile < NT) {
+            int cnt = 0;
+            for_tile_run(bin, N, Lt[tile], Rt[tile], [&](int k0, int k1, float) { cnt += k1 - k0; });
+            tkey[u] = kTileKeys - 1 - min(cnt, kTileKeys - 1);
+            atomicAdd(&tile_hist[tkey[u]], 1);
         }
+    }
+    __syncthreads();
+    block_exclusive_scan(tile_hist, kTileKeys, warp_tot);
+#pragma unroll
+    for (int u = 0; u < kMaxTilesPerThread; ++u)
+        if (tkey[u] >= 0) order[atomicAdd(&tile_hist[tkey[u]], 1)] = (short)(tid + u * nt);
+    __syncthreads();
+
+    // 7. lane pairs walk the tiles in that order; each lane owns two adjacent
+    //    pixels; tau goes to shared memory (the reach array is free now)
+    const int lane_q = tid & (kLanesPerTile - 1);
+    const float K = L.K;
+    for (int i = tid / kLanesPerTile; i < NT; i += nt / kLanesPerTile) {
+        const int tile = order[i];
+        const int o = kTile * tile + 2 * lane_q;
+        float S[2] = {0.f, 0.f}, C[2] = {0.f, 0.f};
+        for_tile_run(bin, N, Lt[tile], Rt[tile], [&](int k0, int k1, float shift) {
+            pair2_segment<COMP>(rec, k0, k1, (float)o + shift, S, C);
+        });
+        if (o < N) tau_s[o] = K * (COMP ? __fsub_rn(S[0], C[0]) : S[0]);
+        if (o + 1 < N) tau_s[o + 1] = K * (COMP ? __fsub_rn(S[1], C[1]) : S[1]);
+    }
+    __syncthreads();
+
+    // 8. tau to HBM in order
+    if (vec && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+        for (int g = tid; 4 * g < N; g += nt)
+            reinterpret_cast<float4*>(out)[g] = reinterpret_cast<const float4*>(tau_s)[g];
+    } else {
+        for (int i = tid; i < N; i += nt) out[i] = tau_s[i];
     }
 }
 
@@ -412,16 +536,18 @@ static size_t global_smem_bytes(int n_pix)
     return sizeof(double4_32a) * (size_t)n_pix + sizeof(int) * (size_t)(n_pix + 1);
 }
 
-// FP32 scatter: hi (and lo when compensated) accumulators with halos.
-static size_t scatter_smem_bytes(int n_pix, int w_max, bool comp)
+// FP32 tile gather: records | bin starts | reach | tile runs.
+static size_t tile_smem_bytes(int n_pix, int w_max)
 {
-    return (comp ? 2 : 1) * sizeof(float) * (size_t)(n_pix + 2 * w_max);
+    const int nt = (n_pix + kTile - 1) / kTile;
+    return sizeof(float4) * (size_t)round_up4(n_pix) + sizeof(int) * (size_t)round_up4(n_pix + 1) +
+           sizeof(int) * (size_t)(n_pix + 2 * w_max) + 3 * sizeof(short) * (size_t)nt;
 }
 
 size_t tau_smem_bytes(int n_pix, int w_max, int precision)
 {
     if (precision == LYA_PREC_F64) return global_smem_bytes(n_pix);
-    return scatter_smem_bytes(n_pix, w_max, precision == LYA_PREC_F32_COMPENSATED);
+    return tile_smem_bytes(n_pix, w_max);
 }
 
 template <typename K>
@@ -438,21 +564,21 @@ static cudaError_t launch_kernel(K kernel, const TauLaunch& L, size_t smem, cuda
 }
 
 template <bool COMP>
-static cudaError_t launch_scatter(const TauLaunch& L, cudaStream_t stream)
+static cudaError_t launch_tile(const TauLaunch& L, cudaStream_t stream)
 {
-    const size_t smem = scatter_smem_bytes(L.n_pix, L.w_max, COMP);
+    const size_t smem = tile_smem_bytes(L.n_pix, L.w_max);
     const int nt = block_threads(L.n_pix);
     const int q = (L.n_pix + nt - 1) / nt;
-    if (q <= 4) return launch_kernel(tau_scatter_kernel<COMP, 4>, L, smem, stream);
-    if (q <= 8) return launch_kernel(tau_scatter_kernel<COMP, 8>, L, smem, stream);
-    return launch_kernel(tau_scatter_kernel<COMP, 16>, L, smem, stream);
+    if (q <= 4) return launch_kernel(tau_tile_kernel<COMP, 4>, L, smem, stream);
+    if (q <= 8) return launch_kernel(tau_tile_kernel<COMP, 8>, L, smem, stream);
+    return launch_kernel(tau_tile_kernel<COMP, 16>, L, smem, stream);
 }
 
 cudaError_t launch_tau(const TauLaunch& L, int precision, cudaStream_t stream)
 {
     switch (precision) {
-    case LYA_PREC_F32_COMPENSATED: return launch_scatter<true>(L, stream);
-    case LYA_PREC_F32_NAIVE: return launch_scatter<false>(L, stream);
+    case LYA_PREC_F32_COMPENSATED: return launch_tile<true>(L, stream);
+    case LYA_PREC_F32_NAIVE: return launch_tile<false>(L, stream);
     case LYA_PREC_F64:
         return launch_kernel(tau_kernel<LYA_PREC_F64>, L, global_smem_bytes(L.n_pix), stream);
     default: return cudaErrorInvalidValue;
