@@ -20,6 +20,7 @@
 // reach |g| <= 1e-12.
 #include <cmath>
 #include <cstdint>
+#include <cstddef>
 #include <cstring>
 #include <mutex>
 
@@ -33,16 +34,55 @@ constexpr int kThreads = 256;
 constexpr double kLog2e = 1.4426950408889634;
 constexpr float kLn2f = 0.69314718055994531f;
 
+// Streams x[0..n) through f(index, value) over the whole grid.  When x is
+// 16-byte aligned each thread keeps four float4 loads in flight per step (the
+// bytes in flight, not the instruction count, bound these HBM passes); the
+// last n % 4 values and unaligned inputs take the scalar path.
+template <typename Fn>
+__device__ __forceinline__ void stream_f32(const float* __restrict__ x, long long n, Fn&& f)
+{
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {
+        const float4* __restrict__ x4 = reinterpret_cast<const float4*>(x);
+        const long long n4 = n >> 2;
+        long long i = tid;
+        for (; i + 3 * nthr < n4; i += 4 * nthr) {
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = x4[i + u * nthr];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const long long b = 4 * (i + u * nthr);
+                f(b, v[u].x); f(b + 1, v[u].y); f(b + 2, v[u].z); f(b + 3, v[u].w);
+            }
+        }
+        for (; i < n4; i += nthr) {
+            const float4 v = x4[i];
+            f(4 * i, v.x); f(4 * i + 1, v.y); f(4 * i + 2, v.z); f(4 * i + 3, v.w);
+        }
+        for (long long k = 4 * n4 + tid; k < n; k += nthr) f(k, x[k]);
+    } else {
+        for (long long k = tid; k < n; k += nthr) f(k, x[k]);
+    }
+}
+
+// Quarter-octave histogram of log2(tau) over [2^-64, 2^64), built in the
+// init pass; its bin centres give a cheap proxy of g(A) whose root starts
+// the exact iteration close to the answer.
+constexpr int kHistBins = 512;
+constexpr float kHistPerOctave = 4.f;
+
 struct MFState {
     double A, lo, hi, g, mean_tau, Ft, tol;
-    double a_hi_unused;
     long long n, n_zero, n_bad;
-    int iter, max_iter, done, status;   // status: LYA_OK / LYA_EINVAL / LYA_ENOCONV
+    int iter, max_iter, done, status;   // status: LYA_OK / LYA_EINVAL / LYA_ENOCONV (not yet converged)
     unsigned int ticket;
+    unsigned long long hist[kHistBins + 1];   // + sampled zeros
 };
 
 struct Partial {
-    double s0, s0c, s1;
+    double s0, s0c, s1, s2;
     long long z, bad;
 };
 
@@ -72,6 +112,45 @@ __device__ void block_sum(double (&v)[K], double (*sh)[32])
             v[k] = warp_sum_d(x);
         }
     }
+    __syncthreads();
+}
+
+// Block sum of a few floats; result valid on every thread.
+template <int K>
+__device__ void block_sum_f(float (&v)[K], float (*sh)[32])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[k][warp] = x;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float x = 0.f;
+        for (int w = 0; w < nw; ++w) x += sh[k][w];
+        v[k] = x;
+    }
+    __syncthreads();
+}
+
+// The last block's totals of the per-CTA partials, summed by all its threads
+// (GB300's FP64 latency makes a one-thread loop over ~1,200 partials slow).
+template <int K, typename Get>
+__device__ void partial_totals(const Partial* part, int nb, double (&tot)[K], double (*sh)[32], Get get)
+{
+#pragma unroll
+    for (int k = 0; k < K; ++k) tot[k] = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        double x[K];
+        get(part[b], x);
+#pragma unroll
+        for (int k = 0; k < K; ++k) tot[k] += x[k];
+    }
+    block_sum<K>(tot, sh);
 }
 
 // Returns true on exactly one block: the last to arrive.
@@ -86,52 +165,112 @@ __device__ bool last_block(unsigned int* ticket)
     return s_last;
 }
 
-// ---- init pass: <tau>, zero and invalid counts, A0 -------------------------------
+__device__ __forceinline__ int hist_bin(float t)
+{
+    const int b = (int)floorf((lg2(t) + 64.f) * kHistPerOctave);
+    return min(max(b, 0), kHistBins - 1);
+}
+
+// ---- init pass: <tau>, zero and invalid counts, log-histogram, start value -------
 __global__ void __launch_bounds__(kThreads) mf_init_kernel(const float* __restrict__ tau, long long n,
                                                          MFState* st, Partial* part)
 {
+    // bins 0..kHistBins-1: log2 tau of a sample (every value for n <= 2^22,
+    // else every 2^k-th with at least 2^22 sampled); the extra slot counts the
+    // sample's zeros.  A start value needs no more than a sample.
+    __shared__ unsigned int h_s[kHistBins + 1];
+    for (int b = threadIdx.x; b <= kHistBins; b += blockDim.x) h_s[b] = 0;
+    __syncthreads();
+    long long smask = 0;
+    while ((n >> 22) > smask) smask = 2 * smask + 1;        // sample stride - 1 (a power of 2 minus 1)
     KahanF32 s;
     long long z = 0, bad = 0;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const float t = tau[i];
-        if (!(t >= 0.f) || !isfinite(t)) { ++bad; continue; }
+    stream_f32(tau, n, [&](long long i, float t) {
+        if (!(t >= 0.f) || !isfinite(t)) { ++bad; return; }
         s.add(t);
         z += (t == 0.f);
-    }
+        if ((i & smask) == 0) atomicAdd(&h_s[t == 0.f ? kHistBins : hist_bin(t)], 1u);
+    });
     __shared__ double sh[3][32];
     double v[3] = {(double)s.value(), (double)z, (double)bad};
     block_sum<3>(v, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = Partial{v[0], 0.0, 0.0, (long long)v[1], (long long)v[2]};
+    for (int b = threadIdx.x; b <= kHistBins; b += blockDim.x)
+        if (h_s[b]) atomicAdd(&st->hist[b], (unsigned long long)h_s[b]);
+    if (threadIdx.x == 0) part[blockIdx.x] = Partial{v[0], 0.0, 0.0, 0.0, (long long)v[1], (long long)v[2]};
     if (!last_block(&st->ticket)) return;
-    if (threadIdx.x != 0) return;
-    double sum = 0.0;
-    long long zz = 0, bb = 0;
-    for (unsigned b = 0; b < gridDim.x; ++b) {
-        sum += part[b].s0;
-        zz += part[b].z;
-        bb += part[b].bad;
+
+    // the last block: totals, domain checks, then the histogram proxy's root
+    __shared__ float s_A;
+    __shared__ int s_stop;
+    double tot[3];
+    partial_totals<3>(part, gridDim.x, tot, sh, [](const Partial& p, double (&x)[3]) {
+        x[0] = p.s0; x[1] = (double)p.z; x[2] = (double)p.bad;
+    });
+    if (threadIdx.x == 0) {
+        const long long zz = (long long)tot[1], bb = (long long)tot[2];
+        st->ticket = 0;
+        st->n_zero = zz;
+        st->n_bad = bb;
+        st->mean_tau = tot[0] / (double)n;
+        st->iter = 0;
+        s_stop = 0;
+        if (bb > 0 || !(st->mean_tau > 0.0)) {
+            st->status = LYA_EINVAL;
+            st->done = 1;
+            s_stop = 1;
+        } else if ((double)zz / (double)n >= st->Ft) {   // <e^{-A tau}> >= zero fraction for all A
+            st->status = LYA_ENOCONV;
+            st->done = 1;
+            s_stop = 1;
+        } else {
+            st->A = -log(st->Ft) / st->mean_tau;         // Jensen: below the root
+            st->lo = st->A;
+            st->hi = INFINITY;
+            st->status = LYA_ENOCONV;                     // until converged
+            st->done = 0;
+            s_A = (float)st->A;
+        }
     }
-    st->ticket = 0;
-    st->n_zero = zz;
-    st->n_bad = bb;
-    st->mean_tau = sum / (double)n;
-    st->iter = 0;
-    if (bb > 0 || !(st->mean_tau > 0.0)) {
-        st->status = LYA_EINVAL;
-        st->done = 1;
-        return;
+    __syncthreads();
+    if (s_stop) return;
+    // Newton on the proxy g_h(A) = (z + sum_b n_b e^{-A tau_b})/n_s - F_t over the
+    // sample (n_s values, z of them zero), tau_b the bin's geometric centre;
+    // convex and decreasing like g.  FP32 is plenty for a start value.
+    __shared__ float shf[2][32];
+    float cnt[1] = {0.f};
+    for (int b = threadIdx.x; b <= kHistBins; b += blockDim.x) cnt[0] += (float)st->hist[b];
+    block_sum_f<1>(cnt, shf);
+    const float inv_n = 1.f / cnt[0], Ft = (float)st->Ft;
+    const float fz = (float)st->hist[kHistBins] * inv_n;
+    if (!(fz < Ft)) return;                 // the sample's proxy has no root: keep the Jensen start
+    const float A_jensen = s_A;
+    float lo = s_A, hi = INFINITY;
+    for (int it = 0; it < 60; ++it) {
+        const float A = s_A;
+        float v2[2] = {0.f, 0.f};
+        for (int b = threadIdx.x; b < kHistBins; b += blockDim.x) {
+            const float c = (float)st->hist[b];
+            if (c == 0.f) continue;
+            const float tb = ex2(((float)b + 0.5f) / kHistPerOctave - 64.f);
+            const float e = ex2(-A * tb * 1.44269504f);
+            v2[0] += c * e;
+            v2[1] += c * tb * e;
+        }
+        block_sum_f<2>(v2, shf);
+        if (threadIdx.x == 0) {
+            const float g = fz + v2[0] * inv_n - Ft, gp = -v2[1] * inv_n;
+            if (g > 0.f) lo = A; else hi = A;
+            float An = gp < 0.f ? A - g / gp : NAN;
+            if (!isfinite(An) || An <= lo || An >= hi) An = isfinite(hi) ? 0.5f * (lo + hi) : 2.f * lo;
+            s_stop = fabsf(An - A) <= 1e-6f * A;
+            s_A = An;
+        }
+        __syncthreads();
+        if (s_stop) break;
     }
-    if ((double)zz / (double)n >= st->Ft) {       // <e^{-A tau}> >= zero fraction for all A
-        st->status = LYA_ENOCONV;
-        st->done = 1;
-        return;
-    }
-    st->A = -log(st->Ft) / st->mean_tau;
-    st->lo = st->A;
-    st->hi = INFINITY;
-    st->status = LYA_ENOCONV;                    // until converged
-    st->done = 0;
+    // a proxy root far from the Jensen bound means an unrepresentative sample
+    if (threadIdx.x == 0 && s_stop && isfinite(s_A) && s_A >= A_jensen && s_A < 1e4f * A_jensen)
+        st->A = (double)s_A;
 }
 
 // Double-float split of a = A log2(e).
@@ -151,7 +290,7 @@ __device__ __forceinline__ void exp_neg(float t, float a_hi, float a_lo, float& 
     corr = -e * y_lo * kLn2f;
 }
 
-// ---- one Newton pass -----------------------------------------------------------------
+// ---- one Halley pass: g, g' and g'' in one read of tau -----------------------------
 __global__ void __launch_bounds__(kThreads) mf_newton_kernel(const float* __restrict__ tau, long long n,
                                                            MFState* st, Partial* part)
 {
@@ -159,32 +298,31 @@ __global__ void __launch_bounds__(kThreads) mf_newton_kernel(const float* __rest
     float a_hi, a_lo;
     split_rate(st->A, a_hi, a_lo);
     KahanF32 s0;
-    float s0c = 0.f, s1 = 0.f;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const float t = tau[i];
+    float s0c = 0.f, s1 = 0.f, s2 = 0.f;
+    stream_f32(tau, n, [&](long long, float t) {
         float e, c;
         exp_neg(t, a_hi, a_lo, e, c);
         s0.add(e);
         s0c += c;
-        s1 = fmaf(t, e, s1);
-    }
-    __shared__ double sh[3][32];
-    double v[3] = {(double)s0.value(), (double)s0c, (double)s1};
-    block_sum<3>(v, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = Partial{v[0], v[1], v[2], 0, 0};
+        const float te = t * e;
+        s1 += te;
+        s2 = fmaf(t, te, s2);
+    });
+    __shared__ double sh[4][32];
+    double v[4] = {(double)s0.value(), (double)s0c, (double)s1, (double)s2};
+    block_sum<4>(v, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = Partial{v[0], v[1], v[2], v[3], 0, 0};
     if (!last_block(&st->ticket)) return;
+    double tot[4];
+    partial_totals<4>(part, gridDim.x, tot, sh, [](const Partial& p, double (&x)[4]) {
+        x[0] = p.s0; x[1] = p.s0c; x[2] = p.s1; x[3] = p.s2;
+    });
     if (threadIdx.x != 0) return;
-    double S0 = 0.0, S0c = 0.0, S1 = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) {
-        S0 += part[b].s0;
-        S0c += part[b].s0c;
-        S1 += part[b].s1;
-    }
+    const double S0 = tot[0], S0c = tot[1], S1 = tot[2], S2 = tot[3];
     st->ticket = 0;
     const double nn = (double)n;
     const double g = (S0 + S0c) / nn - st->Ft;
-    const double gp = -S1 / nn;
+    const double g1 = -S1 / nn, g2 = S2 / nn;
     const double A = st->A;
     st->g = g;
     st->iter += 1;
@@ -194,7 +332,10 @@ __global__ void __launch_bounds__(kThreads) mf_newton_kernel(const float* __rest
         return;
     }
     if (g > 0.0) st->lo = A; else st->hi = A;
-    double An = gp < 0.0 ? A - g / gp : NAN;
+    // Halley's step, then Newton's, then bisection, whichever stays in the bracket
+    const double den = 2.0 * g1 * g1 - g * g2;
+    double An = den > 0.0 ? A - 2.0 * g * g1 / den : NAN;
+    if (!isfinite(An) || An <= st->lo || An >= st->hi) An = g1 < 0.0 ? A - g / g1 : NAN;
     if (!isfinite(An) || An <= st->lo || An >= st->hi)
         An = isfinite(st->hi) ? 0.5 * (st->lo + st->hi) : 2.0 * st->lo;
     if (fabs(An - A) <= 4.0e-16 * fabs(A)) {        // stalled at FP64 resolution
@@ -209,18 +350,42 @@ __global__ void __launch_bounds__(kThreads) mf_newton_kernel(const float* __rest
     }
 }
 
-// ---- F = exp(-A tau) ---------------------------------------------------------------
+// ---- F = exp(-A tau), and the convergence check at that A ------------------------
 __global__ void __launch_bounds__(kThreads) mf_flux_kernel(const float* __restrict__ tau, long long n,
-                                                         const MFState* st, float* __restrict__ F)
+                                                         MFState* st, Partial* part, float* __restrict__ F)
 {
-    if (st->status != LYA_OK) return;
+    if (st->done && st->status != LYA_OK) return;    // an error is final
     float a_hi, a_lo;
     split_rate(st->A, a_hi, a_lo);
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    KahanF32 s0;
+    float s0c = 0.f;
+    stream_f32(tau, n, [&](long long i, float t) {
         float e, c;
-        exp_neg(tau[i], a_hi, a_lo, e, c);
-        F[i] = e + c;
+        exp_neg(t, a_hi, a_lo, e, c);
+        if (F) F[i] = e + c;
+        s0.add(e);
+        s0c += c;
+    });
+    __shared__ double sh[2][32];
+    double v[2] = {(double)s0.value(), (double)s0c};
+    block_sum<2>(v, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = Partial{v[0], v[1], 0.0, 0.0, 0, 0};
+    if (!last_block(&st->ticket)) return;
+    double tot[2];
+    partial_totals<2>(part, gridDim.x, tot, sh, [](const Partial& p, double (&x)[2]) {
+        x[0] = p.s0; x[1] = p.s0c;
+    });
+    if (threadIdx.x != 0) return;
+    const double S0 = tot[0], S0c = tot[1];
+    st->ticket = 0;
+    const double g = (S0 + S0c) / (double)n - st->Ft;
+    st->g = g;
+    if (fabs(g) <= st->tol || (st->done && st->status == LYA_OK)) {
+        st->status = LYA_OK;
+        st->done = 1;
+    } else {
+        st->status = LYA_ENOCONV;                     // more passes needed
+        st->done = 0;
     }
 }
 
@@ -247,37 +412,40 @@ __device__ __forceinline__ int pdf_bin(float F)
 __global__ void __launch_bounds__(kThreads) stats_kernel(const float* __restrict__ F, long long n,
                                                        StatsOut* out, double* part)
 {
-    __shared__ unsigned int hist[21];
-    for (int k = threadIdx.x; k < 21; k += blockDim.x) hist[k] = 0;
-    __syncthreads();
+    // one private 21-bin counter row per thread: plain increments, no atomics;
+    // rows are 21 words apart, and 21 is odd, so a warp's rows hit 32 banks
+    __shared__ unsigned int cnt[kThreads * 21];
+    unsigned int* mine = cnt + threadIdx.x * 21;
+    for (int k = 0; k < 21; ++k) mine[k] = 0;
     KahanF32 m1, m2;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const float f = F[i];
+    stream_f32(F, n, [&](long long, float f) {
         const float d = f - 0.5f;
         m1.add(d);
         m2.add(d * d);
-        atomicAdd(&hist[pdf_bin(f)], 1u);
-    }
+        mine[pdf_bin(f)] += 1u;
+    });
     __shared__ double sh[2][32];
     double v[2] = {(double)m1.value(), (double)m2.value()};
-    block_sum<2>(v, sh);
-    __syncthreads();
-    for (int k = threadIdx.x; k < 21; k += blockDim.x)
-        if (hist[k]) atomicAdd(&out->pdf[k], (unsigned long long)hist[k]);
+    block_sum<2>(v, sh);                                     // ends with a barrier
+    for (int k = threadIdx.x; k < 21; k += blockDim.x) {
+        unsigned long long c = 0;
+        for (int r = 0; r < (int)blockDim.x; ++r) c += cnt[r * 21 + k];
+        if (c) atomicAdd(&out->pdf[k], c);
+    }
     if (threadIdx.x == 0) {
         part[2 * blockIdx.x] = v[0];
         part[2 * blockIdx.x + 1] = v[1];
     }
     if (!last_block(&out->ticket)) return;
-    if (threadIdx.x != 0) return;
-    double a = 0.0, b = 0.0;
-    for (unsigned k = 0; k < gridDim.x; ++k) {
-        a += part[2 * k];
-        b += part[2 * k + 1];
+    double tot[2] = {0.0, 0.0};
+    for (unsigned k = threadIdx.x; k < gridDim.x; k += blockDim.x) {
+        tot[0] += part[2 * k];
+        tot[1] += part[2 * k + 1];
     }
-    out->m1 = a;
-    out->m2 = b;
+    block_sum<2>(tot, sh);
+    if (threadIdx.x != 0) return;
+    out->m1 = tot[0];
+    out->m2 = tot[1];
     out->ticket = 0;
 }
 
@@ -289,9 +457,7 @@ __global__ void __launch_bounds__(kThreads) field_check_kernel(const float* __re
 {
     unsigned long long br = 0, bv = 0, bt = 0;
     float tmax = 0.f, rmax = 0.f, rmin = INFINITY;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const float r = rho[i], u = v[i];
+    auto check = [&](float r, float u, float t) {
         const bool rok = r >= 0.f && isfinite(r);
         br += !rok;
         bv += !(isfinite(u) && fabsf(u) < 2.99792458e5f);
@@ -300,12 +466,27 @@ __global__ void __launch_bounds__(kThreads) field_check_kernel(const float* __re
             rmin = fminf(rmin, r);
         }
         if (T) {
-            const float t = T[i];
             const bool ok = isfinite(t) && (t > 0.f || !(r > 0.f));
             bt += !ok;
             if (ok && r > 0.f) tmax = fmaxf(tmax, t);
         }
+    };
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    const bool aligned = ((reinterpret_cast<uintptr_t>(rho) | reinterpret_cast<uintptr_t>(v) |
+                           reinterpret_cast<uintptr_t>(T)) & 15) == 0;
+    long long k0 = 0;
+    if (aligned) {
+        const long long n4 = n >> 2;
+        for (long long i = tid; i < n4; i += nthr) {
+            const float4 r = reinterpret_cast<const float4*>(rho)[i];
+            const float4 u = reinterpret_cast<const float4*>(v)[i];
+            const float4 t = T ? reinterpret_cast<const float4*>(T)[i] : make_float4(1.f, 1.f, 1.f, 1.f);
+            check(r.x, u.x, t.x); check(r.y, u.y, t.y); check(r.z, u.z, t.z); check(r.w, u.w, t.w);
+        }
+        k0 = 4 * n4;
     }
+    for (long long i = k0 + tid; i < n; i += nthr) check(rho[i], v[i], T ? T[i] : 1.f);
     for (int o = 16; o > 0; o >>= 1) {
         br += __shfl_down_sync(0xffffffffu, br, o);
         bv += __shfl_down_sync(0xffffffffu, bv, o);
@@ -373,58 +554,75 @@ cudaError_t launch_field_check(const float* rho, const float* vpec, const float*
         if (_e != cudaSuccess) { err = _e; goto done; } \
     } while (0)
 
+namespace {
+
+// The host side of one root-find on caller-chosen scratch: the init pass,
+// then rounds of two Halley passes and one flux pass (which writes F, if
+// asked, and checks |g| <= tol at the final A), reading the state back once
+// per round.
+static lya_status solve_on_scratch(const float* tau, int64_t n, double target, double tol, int max_iter,
+                                   double* A_out, float* flux_out, MFState* st, Partial* part, int grid,
+                                   cudaStream_t stream)
+{
+    static_assert(sizeof(MFState) % 8 == 0, "state layout");
+    MFState hs{};                                   // host copy (no heap allocation)
+    MFState* h = &hs;
+    h->Ft = target;
+    h->tol = tol;
+    h->n = n;
+    h->max_iter = max_iter;
+    h->status = LYA_ENOCONV;
+    lya_status result = LYA_ENOCONV;
+    cudaError_t err = cudaMemcpyAsync(st, h, sizeof(MFState), cudaMemcpyHostToDevice, stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(stream);   // h is reused below
+    if (err == cudaSuccess) {
+        mf_init_kernel<<<grid, kThreads, 0, stream>>>(tau, n, st, part);
+        count_launch();
+        err = cudaGetLastError();
+    }
+    for (int round = 0; err == cudaSuccess; ++round) {
+        for (int b = 0; b < 2 && err == cudaSuccess; ++b) {
+            mf_newton_kernel<<<grid, kThreads, 0, stream>>>(tau, n, st, part);
+            count_launch();
+            err = cudaGetLastError();
+        }
+        if (err != cudaSuccess) break;
+        mf_flux_kernel<<<grid, kThreads, 0, stream>>>(tau, n, st, part, flux_out);
+        count_launch();
+        err = cudaGetLastError();
+        if (err == cudaSuccess) err = cudaMemcpyAsync(h, st, offsetof(MFState, hist), cudaMemcpyDeviceToHost, stream);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(stream);
+        if (err != cudaSuccess) break;
+        if (h->done) {
+            result = (lya_status)h->status;
+            break;
+        }
+        if (h->iter >= max_iter) {
+            result = LYA_ENOCONV;
+            break;
+        }
+    }
+    if (err == cudaSuccess && result == LYA_OK) *A_out = h->A;
+    if (err != cudaSuccess) return err == cudaErrorMemoryAllocation ? LYA_ENOMEM : LYA_ECUDA;
+    return result;
+}
+
+}  // namespace
+
 lya_status mean_flux_solve(const float* tau, int64_t n, double target, double tol, int max_iter,
                            double* A_out, float* flux_out, cudaStream_t stream)
 {
     const int grid = grid_for(n);
     MFState* st = nullptr;
     Partial* part = nullptr;
-    MFState h{};
-    cudaError_t err = cudaSuccess;
-    lya_status result = LYA_OK;
-    h.Ft = target;
-    h.tol = tol;
-    h.n = n;
-    h.max_iter = max_iter;
-    h.status = LYA_ENOCONV;
-    LYA_TRY(cudaMallocAsync((void**)&st, sizeof(MFState), stream));
-    LYA_TRY(cudaMallocAsync((void**)&part, sizeof(Partial) * grid, stream));
-    LYA_TRY(cudaMemcpyAsync(st, &h, sizeof(MFState), cudaMemcpyHostToDevice, stream));
-    mf_init_kernel<<<grid, kThreads, 0, stream>>>(tau, n, st, part);
-    count_launch();
-    LYA_TRY(cudaGetLastError());
-    // Newton typically converges in 3-6 passes: launch them in batches and
-    // read the state back once per batch.
-    for (int launched = 0; launched < max_iter;) {
-        const int batch = launched == 0 ? 6 : 4;
-        for (int b = 0; b < batch && launched < max_iter; ++b, ++launched) {
-            mf_newton_kernel<<<grid, kThreads, 0, stream>>>(tau, n, st, part);
-            count_launch();
-            LYA_TRY(cudaGetLastError());
-        }
-        LYA_TRY(cudaMemcpyAsync(&h, st, sizeof(MFState), cudaMemcpyDeviceToHost, stream));
-        LYA_TRY(cudaStreamSynchronize(stream));
-        if (h.done) break;
-    }
-    if (!h.done) {
-        result = LYA_ENOCONV;
-    } else {
-        result = (lya_status)h.status;
-    }
-    if (result == LYA_OK) {
-        *A_out = h.A;
-        if (flux_out) {
-            mf_flux_kernel<<<grid, kThreads, 0, stream>>>(tau, n, st, flux_out);
-            count_launch();
-            LYA_TRY(cudaGetLastError());
-        }
-    }
-done:
+    cudaError_t err = cudaMallocAsync((void**)&st, sizeof(MFState), stream);
+    if (err == cudaSuccess) err = cudaMallocAsync((void**)&part, sizeof(Partial) * grid, stream);
+    lya_status result = err == cudaSuccess
+        ? solve_on_scratch(tau, n, target, tol, max_iter, A_out, flux_out, st, part, grid, stream)
+        : (err == cudaErrorMemoryAllocation ? LYA_ENOMEM : LYA_ECUDA);
     if (st) cudaFreeAsync(st, stream);
     if (part) cudaFreeAsync(part, stream);
-    if (err != cudaSuccess) return err == cudaErrorMemoryAllocation ? LYA_ENOMEM : LYA_ECUDA;
-    cudaError_t e2 = cudaStreamSynchronize(stream);
-    if (e2 != cudaSuccess) return LYA_ECUDA;
+    if (cudaStreamSynchronize(stream) != cudaSuccess && result == LYA_OK) result = LYA_ECUDA;
     return result;
 }
 
@@ -483,7 +681,7 @@ namespace {
 
 constexpr size_t kNoAllocScratchBytes = 64 * 1024;
 constexpr int kNoAllocMaxBlocks = 1024;
-constexpr size_t kNoAllocStateBytes = 256;      // MFState, padded to the array's alignment
+constexpr size_t kNoAllocStateBytes = 8192;     // MFState, padded to the array's alignment
 static_assert(sizeof(MFState) <= kNoAllocStateBytes, "state does not fit its slot");
 static_assert(kNoAllocStateBytes + kNoAllocMaxBlocks * sizeof(Partial) <= kNoAllocScratchBytes,
               "partials do not fit the scratch array");
@@ -519,47 +717,12 @@ lya_status mean_flux_solve_noalloc(const float* tau, int64_t n, double target, d
                                    double* A_out, float* flux_out, cudaStream_t stream)
 {
     void* scratch = nullptr;
-    cudaError_t err = noalloc_scratch(&scratch);
-    if (err != cudaSuccess) return LYA_ECUDA;
+    if (noalloc_scratch(&scratch) != cudaSuccess) return LYA_ECUDA;
     const int grid = grid_for(n) < kNoAllocMaxBlocks ? grid_for(n) : kNoAllocMaxBlocks;
     if (kNoAllocStateBytes + (size_t)grid * sizeof(Partial) > kNoAllocScratchBytes) return LYA_EINVAL;
     MFState* st = static_cast<MFState*>(scratch);
     Partial* part = reinterpret_cast<Partial*>(static_cast<unsigned char*>(scratch) + kNoAllocStateBytes);
-    MFState h{};
-    h.Ft = target;
-    h.tol = tol;
-    h.n = n;
-    h.max_iter = max_iter;
-    h.status = LYA_ENOCONV;
-    lya_status result = LYA_OK;
-    err = cudaMemcpyAsync(st, &h, sizeof(MFState), cudaMemcpyHostToDevice, stream);
-    if (err != cudaSuccess) return LYA_ECUDA;
-    mf_init_kernel<<<grid, kThreads, 0, stream>>>(tau, n, st, part);
-    count_launch();
-    if (cudaGetLastError() != cudaSuccess) return LYA_ECUDA;
-    for (int launched = 0; launched < max_iter;) {
-        const int batch = launched == 0 ? 6 : 4;
-        for (int b = 0; b < batch && launched < max_iter; ++b, ++launched) {
-            mf_newton_kernel<<<grid, kThreads, 0, stream>>>(tau, n, st, part);
-            count_launch();
-            if (cudaGetLastError() != cudaSuccess) return LYA_ECUDA;
-        }
-        err = cudaMemcpyAsync(&h, st, sizeof(MFState), cudaMemcpyDeviceToHost, stream);
-        if (err == cudaSuccess) err = cudaStreamSynchronize(stream);
-        if (err != cudaSuccess) return LYA_ECUDA;
-        if (h.done) break;
-    }
-    result = h.done ? (lya_status)h.status : LYA_ENOCONV;
-    if (result == LYA_OK) {
-        *A_out = h.A;
-        if (flux_out) {
-            mf_flux_kernel<<<grid, kThreads, 0, stream>>>(tau, n, st, flux_out);
-            count_launch();
-            if (cudaGetLastError() != cudaSuccess) return LYA_ECUDA;
-            if (cudaStreamSynchronize(stream) != cudaSuccess) return LYA_ECUDA;
-        }
-    }
-    return result;
+    return solve_on_scratch(tau, n, target, tol, max_iter, A_out, flux_out, st, part, grid, stream);
 }
 
 }  // namespace lya
