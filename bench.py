@@ -40,6 +40,12 @@ METRIC = "tau-skewer pixels/s on 1 GB300 at |dF|<=1e-5 vs FP64 oracle"
 UNIT = "pixels/s"
 WORKLOAD = "gpc_box_65536x4096_z2.5"
 ALG_BYTES_PER_PX = 16          # rho, vpec, T read (12 B) + tau written (4 B)
+# DRAM bytes of one tau-kernel launch per skewer, from the ncu capture in
+# profiles/tau_tile_kernel_gpc_8192x4096.md (8,192 skewers, scaled by skewer
+# count).  Valid only for the kernel source it was taken on: reported as null
+# once paper_1105_4747_gb300/csrc/tau_extract.cu changes.
+TAU_DRAM_BYTES_PER_SKEWER = (402.873856e6 + 75.516672e6) / 8192
+TAU_PROFILED_SOURCE_SHA1 = "9dc5999d831d8a857dfd5937aecb47cf23bf2442"
 
 
 def workload_config(spec, S, extra=None):
@@ -302,8 +308,12 @@ def run_ours(args):
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     achieved = ALG_BYTES_PER_PX * n_px / (tau_ms / 1e3) / 1e9
+    import hashlib
+    src = os.path.join(ROOT, "paper_1105_4747_gb300", "csrc", "tau_extract.cu")
+    same_kernel = hashlib.sha1(open(src, "rb").read()).hexdigest() == TAU_PROFILED_SOURCE_SHA1
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak,
+                "traffic": TAU_DRAM_BYTES_PER_SKEWER * S if same_kernel else None,
                 "kernel": "tau_tile_kernel<compensated,8>", "kernel_ms": tau_ms,
                 "peak_source": "measured" if peaks else "fallback",
                 "alg_bytes_per_launch": ALG_BYTES_PER_PX * n_px}

@@ -496,11 +496,17 @@ __global__ void __launch_bounds__(512, MAXQ <= 8 ? 2 : 1) tau_tile_kernel(const 
         if (tkey[u] >= 0) order[atomicAdd(&tile_hist[tkey[u]], 1)] = (short)(tid + u * nt);
     __syncthreads();
 
-    // 7. lane pairs walk the tiles in that order; each lane owns two adjacent
-    //    pixels; tau goes to shared memory (the reach array is free now)
+    // 7. lane pairs walk the tiles in that order (snaking across rounds); each
+    //    lane owns two adjacent pixels; tau goes to shared memory (the reach
+    //    array is free now)
     const int lane_q = tid & (kLanesPerTile - 1);
     const float K = L.K;
-    for (int i = tid / kLanesPerTile; i < NT; i += nt / kLanesPerTile) {
+    const int npairs = nt / kLanesPerTile, pair = tid / kLanesPerTile;
+    for (int round = 0; round * npairs < NT; ++round) {
+        // snake order: alternate rounds run the largest tiles on the last
+        // pairs, so every warp's total work evens out across rounds
+        const int i = round * npairs + ((round & 1) ? npairs - 1 - pair : pair);
+        if (i >= NT) continue;
         const int tile = order[i];
         const int o = kTile * tile + 2 * lane_q;
         float S[2] = {0.f, 0.f}, C[2] = {0.f, 0.f};

@@ -311,3 +311,36 @@ def test_gpc_full_size_sampled_parity(lya, orc, gpc_field, gamma):
     st_o = orc.flux_stats(F.cpu().numpy())
     np.testing.assert_array_equal(st.pdf, st_o.pdf)
     assert st.mean_flux == pytest.approx(ls.GPC_4096_FT, abs=1e-6)
+
+
+def test_precision_study_1024_skewers(lya, orc, gpc_field, capsys):
+    """Precision study on 1,024 random skewers of the 1 h^-1 Gpc field: FP32
+    compensated, FP32 naive and the FP64 kernel against the FP64 oracle.
+    Reports max tau relative error (A tau > 1e-6), max |dF| (each side with
+    its own A over the subset) and the per-skewer column (sum of tau) error."""
+    import torch
+    spec, field = gpc_field
+    n_pick, seed = ls.GPC_4096_PRECISION_SUBSET
+    ids = ls.random_subset(ls.GPC_4096_SKEWERS, n_pick, seed)
+    rho, v, t = ls.skewers(spec, ids)
+    tau_o = orc.tau(oparams(orc, spec), rho, v, t)
+    A_o, _ = orc.rescale(tau_o, ls.GPC_4096_FT)
+    F_o = orc.flux(tau_o, A_o)
+    col_o = tau_o.sum(axis=1)
+    rows = []
+    for prec, name in [(0, "f32 compensated"), (1, "f32 naive"), (2, "f64")]:
+        tau = lya.extract_skewers(field, lya.ExtractParams(precision=prec), ids=ids)
+        A_g, F = lya.rescale_mean_flux(tau, ls.GPC_4096_FT)
+        torch.cuda.synchronize()
+        tg = tau.double().cpu().numpy()
+        mask = A_o * tau_o > TAU_FLOOR
+        rel = float((np.abs(tg - tau_o)[mask] / tau_o[mask]).max())
+        dF = float(np.abs(F.cpu().numpy() - F_o).max())
+        dcol = float((np.abs(tg.sum(axis=1) - col_o) / col_o).max())
+        rows.append((name, rel, dF, dcol, A_g / A_o - 1))
+        assert rel <= TAU_RTOL and dF <= F_ATOL
+    with capsys.disabled():
+        print("\nprecision study, 1,024 skewers x 4,096 px (1 h^-1 Gpc, z = 2.5)")
+        print(f"{'variant':18s} {'max tau rel':>12s} {'max |dF|':>10s} {'max col rel':>12s} {'A/A_o - 1':>11s}")
+        for name, rel, dF, dcol, dA in rows:
+            print(f"{name:18s} {rel:12.3e} {dF:10.3e} {dcol:12.3e} {dA:11.3e}")
