@@ -40,19 +40,22 @@ METRIC = "tau-skewer pixels/s on 1 GB300 at |dF|<=1e-5 vs FP64 oracle"
 UNIT = "pixels/s"
 WORKLOAD = "gpc_box_65536x4096_z2.5"
 ALG_BYTES_PER_PX = 16          # rho, vpec, T read (12 B) + tau written (4 B)
-# DRAM bytes of one tau-kernel launch per skewer, from the ncu capture in
-# profiles/tau_tile_kernel_gpc_8192x4096.md (8,192 skewers, scaled by skewer
-# count).  Valid only for the kernel source it was taken on: reported as null
-# once paper_1105_4747_gb300/csrc/tau_extract.cu changes.
-TAU_DRAM_BYTES_PER_SKEWER = (402.873856e6 + 75.516672e6) / 8192
-TAU_PROFILED_SOURCE_SHA1 = "9dc5999d831d8a857dfd5937aecb47cf23bf2442"
+# DRAM bytes of one tau-kernel launch per skewer, from the ncu captures in
+# profiles/ (8,192 skewers of the Gpc workload; 262,144 rows of the grid),
+# scaled by the number of skewers.  Valid only for the kernel source they were
+# taken on: reported as null once paper_1105_4747_gb300/csrc/tau_extract.cu
+# changes.
+TAU_DRAM_BYTES_PER_SKEWER = {"gpc": (402.725632e6 + 76.099328e6) / 8192,
+                             "grid1536": (4.832250e9 + 1.551512e9) / 262144}
+TAU_PROFILED_SOURCE_SHA1 = "baa23b9688d05ea3c8c3be43ac9154216f7b199f"
 
 
-def workload_config(spec, S, extra=None):
-    c = {"workload": WORKLOAD, "n_skewers": S, "n_pix": spec.n_pix, "box_mpc_h": spec.box,
-         "z": spec.z, "T": "stored", "gamma": spec.gamma, "target_mean_flux": ls.GPC_4096_FT,
+def workload_config(spec, S, extra=None, grid=False):
+    c = {"workload": "grid_1536cubed_z2.3" if grid else WORKLOAD, "n_skewers": S, "n_pix": spec.n_pix,
+         "box_mpc_h": spec.box, "z": spec.z, "T": "stored", "gamma": spec.gamma,
+         "target_mean_flux": ls.GRID_1536_FT if grid else ls.GPC_4096_FT,
          "precision": "f32 pairs, compensated sum; f64 root-find",
-         "l2": "inputs 3.2 GB > 129 MB L2: no flush between steps"}
+         "l2": ("inputs 43.5 GB" if grid else "inputs 3.2 GB") + " > 129 MB L2: no flush between steps"}
     if extra:
         c.update(extra)
     return c
@@ -222,10 +225,13 @@ def run_reference(args):
 # our arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
-    spec = ls.GPC_4096
-    S = ls.GPC_4096_SKEWERS if args.skewers is None else args.skewers
-    # host generation first: the spawn pool starts before any CUDA call
-    rho, v, t = ls.skewers_parallel(spec, np.arange(S))
+    grid = args.workload == "grid1536"
+    spec = ls.GRID_1536 if grid else ls.GPC_4096
+    S = (ls.GRID_1536_ROWS if grid else ls.GPC_4096_SKEWERS) if args.skewers is None else args.skewers
+    target = ls.GRID_1536_FT if grid else ls.GPC_4096_FT
+    if not grid:
+        # host generation first: the spawn pool starts before any CUDA call
+        rho, v, t = ls.skewers_parallel(spec, np.arange(S))
     import torch
     world, rank, local = dist_setup()
     import __graft_entry__
@@ -233,7 +239,11 @@ def run_ours(args):
     import paper_1105_4747_gb300 as lya
 
     stream = torch.cuda.current_stream()
-    field = lya.Field(rho, v, t, box=spec.box, z=spec.z)
+    if grid:
+        rho, v, t = ls.grid_on_device(spec, S, torch)       # 43.5 GB on the device
+        field = lya.Field(rho, v, t, box=spec.box, z=spec.z, borrow=True)
+    else:
+        field = lya.Field(rho, v, t, box=spec.box, z=spec.z)
     params = lya.ExtractParams(t_mode=0, precision=lya.PREC_F32_COMPENSATED)
     tau = torch.empty((S, spec.n_pix), dtype=torch.float32, device="cuda")
     F = torch.empty_like(tau)
@@ -245,7 +255,7 @@ def run_ours(args):
         lya.extract_skewers(field, params, out=tau)
         if ev is not None:
             ev[1].record(stream)
-        A, _ = lya.rescale_mean_flux(tau, ls.GPC_4096_FT, flux_out=F)
+        A, _ = lya.rescale_mean_flux(tau, target, flux_out=F)
         st = lya.flux_stats(F)
         return A, st
 
@@ -276,7 +286,7 @@ def run_ours(args):
 
     # end to end through the public API: host inputs in, host flux out
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not grid:
         rho_h = torch.from_numpy(rho).pin_memory()
         v_h = torch.from_numpy(v).pin_memory()
         t_h = torch.from_numpy(t).pin_memory()
@@ -285,7 +295,7 @@ def run_ours(args):
         def e2e_step():
             field.load(rho_h, v_h, t_h)
             lya.extract_skewers(field, params, out=tau)
-            lya.rescale_mean_flux(tau, ls.GPC_4096_FT, flux_out=F)
+            lya.rescale_mean_flux(tau, target, flux_out=F)
             lya.flux_stats(F)
             F_h.copy_(F, non_blocking=True)
 
@@ -313,13 +323,13 @@ def run_ours(args):
     same_kernel = hashlib.sha1(open(src, "rb").read()).hexdigest() == TAU_PROFILED_SOURCE_SHA1
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak,
-                "traffic": TAU_DRAM_BYTES_PER_SKEWER * S if same_kernel else None,
+                "traffic": TAU_DRAM_BYTES_PER_SKEWER[args.workload] * S if same_kernel else None,
                 "kernel": "tau_tile_kernel<compensated,8>", "kernel_ms": tau_ms,
                 "peak_source": "measured" if peaks else "fallback",
                 "alg_bytes_per_launch": ALG_BYTES_PER_PX * n_px}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not grid:
         cpu = oracle_timing(spec, args.cpu_seconds)
 
     if rank == 0:
@@ -327,7 +337,7 @@ def run_ours(args):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": workload_config(spec, S, {"parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
-                                                    "A": A, "mean_flux": st.mean_flux}),
+                                                    "A": A, "mean_flux": st.mean_flux}, grid),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk}
         print(json.dumps(line), flush=True)
@@ -345,6 +355,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--skewers", type=int, default=None, help="fewer skewers (debug only)")
+    ap.add_argument("--workload", choices=["gpc", "grid1536"], default="gpc",
+                    help="gpc: 65,536 x 4,096 px (the metric's workload); grid1536: all rows of a 1536^3 grid")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -165,3 +165,58 @@ def skewers_parallel(spec: FieldSpec, ids, with_temp: bool = True, workers: int 
             if with_temp:
                 temp[lo:lo + r.shape[0]] = t
     return rho, vpec, temp
+
+
+# ---- rows of a large periodic grid --------------------------------------------------
+# A 1536^3 grid has 2.36 million rows: drawing each one from its own seed on
+# the host would take minutes and 43 GB of host memory.  Row r of such a grid
+# is instead pool row (r mod P), cyclically shifted by ((r div P) * 997) mod N
+# pixels.  A periodic shift of a periodic realisation is itself a valid
+# realisation, so every row is a skewer with the stated statistics, distinct
+# from every other row.
+GRID_POOL_ROWS = 16384
+
+
+def grid_row_shift(row_ids, n_pix: int, pool: int = GRID_POOL_ROWS) -> np.ndarray:
+    row_ids = np.asarray(row_ids, dtype=np.int64)
+    return ((row_ids // pool) * 997) % n_pix
+
+
+def grid_rows(spec: FieldSpec, row_ids, pool: int = GRID_POOL_ROWS, with_temp: bool = True):
+    """Host arrays of the given grid rows (same layout as :func:`skewers`)."""
+    row_ids = np.asarray(row_ids, dtype=np.int64).ravel()
+    base, shift = row_ids % pool, grid_row_shift(row_ids, spec.n_pix, pool)
+    r, v, t = skewers(spec, base, with_temp=with_temp)
+    out = []
+    for a in (r, v, t):
+        if a is None:
+            out.append(None)
+            continue
+        b = np.empty_like(a)
+        for k, s in enumerate(shift):
+            b[k] = np.roll(a[k], int(s))
+        out.append(b)
+    return tuple(out)
+
+
+def grid_on_device(spec: FieldSpec, n_rows: int, torch, device="cuda", pool: int = GRID_POOL_ROWS,
+                   with_temp: bool = True, chunk: int = 8192):
+    """Build all n_rows grid rows on the device (torch tensors [n_rows][N]).
+
+    The pool is drawn on the host (parallel, seeded per row) and copied once;
+    the rows are gathered from it on the device, chunk by chunk.
+    """
+    N = spec.n_pix
+    pr, pv, pt = skewers_parallel(spec, np.arange(pool), with_temp=with_temp)
+    pools = [torch.from_numpy(a).to(device) for a in (pr, pv, pt) if a is not None]
+    outs = [torch.empty((n_rows, N), dtype=torch.float32, device=device) for _ in pools]
+    cols = torch.arange(N, device=device)
+    for lo in range(0, n_rows, chunk):
+        rows = torch.arange(lo, min(lo + chunk, n_rows), device=device)
+        base = rows % pool
+        shift = ((rows // pool) * 997) % N
+        idx = (cols[None, :] - shift[:, None]) % N          # out[i] = pool[(i - s) mod N]
+        for src, dst in zip(pools, outs):
+            dst[lo:lo + rows.numel()] = torch.gather(src[base], 1, idx)
+    del pools
+    return tuple(outs) + ((None,) if not with_temp else ())
