@@ -187,6 +187,22 @@ lya_status lya_rescale_mean_flux_noalloc(const float* tau, int64_t n, double tar
                                          float* flux_out, void* stream);
 
 /*
+ * Per-device shares of the mean-flux root-find (Sec. 2.3) when one request's
+ * pixels are split over several devices or processes: each computes its
+ * share, the caller sums the shares over all parts (an all-reduce of three
+ * numbers) and steps A itself, then writes F with lya_flux_at.
+ *   lya_tau_moments:    out = { sum tau, number of tau == 0, number of
+ *                       negative or non-finite tau } over n device values.
+ *   lya_mean_flux_sums: out = { sum e, sum tau e, sum tau^2 e }, e = exp(-A tau),
+ *                       in FP64 (the terms in FP32, see lya_rescale_mean_flux).
+ *   lya_flux_at:        flux_out[i] = exp(-A tau[i]) (device, n floats).
+ * The first two synchronise the stream; A must be finite and >= 0.
+ */
+lya_status lya_tau_moments(const float* tau, int64_t n, double out[3], void* stream);
+lya_status lya_mean_flux_sums(const float* tau, int64_t n, double A, double out[3], void* stream);
+lya_status lya_flux_at(const float* tau, int64_t n, double A, float* flux_out, void* stream);
+
+/*
  * Flux statistics (Sec. 2.3, Sec. 5.2) over n device values F: mean,
  * population variance, tau_eff = -ln<F> and the 21-bin PDF with bin k holding
  * (2k-1)/40 <= F < (2k+1)/40 (clamped to [0, 20]); the bin decision is exact

@@ -17,10 +17,14 @@ from ._binding import (  # noqa: F401
     FluxStats,
     LyaError,
     extract_skewers,
+    flux_at,
     flux_stats,
+    mean_flux_sums,
+    tau_moments,
     kernel_launches,
     library_path,
     load_library,
     rescale_mean_flux,
     rescale_mean_flux_noalloc,
 )
+from .distributed import rescale_mean_flux_distributed  # noqa: F401,E402

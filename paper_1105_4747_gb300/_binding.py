@@ -89,9 +89,13 @@ def load_library():
         lib.lya_rescale_mean_flux.argtypes = [vp, i64, d, d, i32, ctypes.POINTER(d), vp, vp]
         lib.lya_rescale_mean_flux_noalloc.argtypes = [vp, i64, d, d, i32, ctypes.POINTER(d), vp, vp]
         lib.lya_flux_stats.argtypes = [vp, i64, ctypes.POINTER(_FluxStats), vp]
+        lib.lya_tau_moments.argtypes = [vp, i64, ctypes.POINTER(d), vp]
+        lib.lya_mean_flux_sums.argtypes = [vp, i64, d, ctypes.POINTER(d), vp]
+        lib.lya_flux_at.argtypes = [vp, i64, d, vp, vp]
         for name in ("lya_create_field", "lya_field_load", "lya_destroy_field", "lya_field_status",
                      "lya_field_shape", "lya_extract_skewers", "lya_rescale_mean_flux",
-                     "lya_rescale_mean_flux_noalloc", "lya_flux_stats"):
+                     "lya_rescale_mean_flux_noalloc", "lya_flux_stats", "lya_tau_moments",
+                     "lya_mean_flux_sums", "lya_flux_at"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -285,6 +289,36 @@ def rescale_mean_flux_noalloc(tau, target: float, flux_out, tol: float = 1e-12, 
         flux_out.data_ptr() if flux_out is not None else None, _stream_handle(stream)),
         "lya_rescale_mean_flux_noalloc")
     return A.value
+
+
+def tau_moments(tau, stream=None):
+    """(sum tau, number of zeros, number of invalid values) of device values (lya_tau_moments)."""
+    _require_cuda_f32(tau, "tau")
+    out = (ctypes.c_double * 3)()
+    _check(load_library().lya_tau_moments(tau.data_ptr(), tau.numel(), out, _stream_handle(stream)),
+           "lya_tau_moments")
+    return tuple(out)
+
+
+def mean_flux_sums(tau, A: float, stream=None):
+    """(sum e, sum tau e, sum tau^2 e), e = exp(-A tau), over device values (lya_mean_flux_sums)."""
+    _require_cuda_f32(tau, "tau")
+    out = (ctypes.c_double * 3)()
+    _check(load_library().lya_mean_flux_sums(tau.data_ptr(), tau.numel(), float(A), out,
+                                             _stream_handle(stream)), "lya_mean_flux_sums")
+    return tuple(out)
+
+
+def flux_at(tau, A: float, out=None, stream=None):
+    """F = exp(-A tau) on the device for a given A (lya_flux_at)."""
+    _require_cuda_f32(tau, "tau")
+    F = out if out is not None else _torch().empty_like(tau)
+    _require_cuda_f32(F, "out")
+    if F.numel() != tau.numel():
+        raise ValueError("out must have as many elements as tau")
+    _check(load_library().lya_flux_at(tau.data_ptr(), tau.numel(), float(A), F.data_ptr(),
+                                      _stream_handle(stream)), "lya_flux_at")
+    return F
 
 
 @dataclass

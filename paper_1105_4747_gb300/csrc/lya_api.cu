@@ -332,6 +332,24 @@ lya_status lya_rescale_mean_flux_noalloc(const float* tau, int64_t n, double tar
                                         static_cast<cudaStream_t>(stream));
 }
 
+lya_status lya_tau_moments(const float* tau, int64_t n, double out[3], void* stream)
+{
+    if (!tau || n <= 0 || !out) return LYA_EINVAL;
+    return lya::tau_moments_run(tau, n, out, static_cast<cudaStream_t>(stream));
+}
+
+lya_status lya_mean_flux_sums(const float* tau, int64_t n, double A, double out[3], void* stream)
+{
+    if (!tau || n <= 0 || !out || !(A >= 0.0) || !std::isfinite(A)) return LYA_EINVAL;
+    return lya::mean_flux_sums_run(tau, n, A, out, static_cast<cudaStream_t>(stream));
+}
+
+lya_status lya_flux_at(const float* tau, int64_t n, double A, float* flux_out, void* stream)
+{
+    if (!tau || n <= 0 || !flux_out || !(A >= 0.0) || !std::isfinite(A)) return LYA_EINVAL;
+    return lya::flux_at_run(tau, n, A, flux_out, static_cast<cudaStream_t>(stream));
+}
+
 lya_status lya_flux_stats(const float* flux, int64_t n, lya_flux_stats_t* out, void* stream)
 {
     if (!flux || n <= 0 || !out) return LYA_EINVAL;

@@ -56,6 +56,12 @@ lya_status mean_flux_solve_noalloc(const float* tau, int64_t n, double target, d
                                    int max_iter, double* A_out, float* flux_out,
                                    cudaStream_t stream);
 
+// Per-device shares of a root-find split over devices: tau moments (sum,
+// zeros, invalid), the sums at a given A, and F at a given A.
+lya_status tau_moments_run(const float* tau, int64_t n, double* out3, cudaStream_t stream);
+lya_status mean_flux_sums_run(const float* tau, int64_t n, double A, double* out3, cudaStream_t stream);
+lya_status flux_at_run(const float* tau, int64_t n, double A, float* flux, cudaStream_t stream);
+
 // Flux statistics (Sec. 2.3, 5.2) over n device flux values.
 lya_status flux_stats_run(const float* flux, int64_t n, lya_flux_stats_t* out,
                           cudaStream_t stream);

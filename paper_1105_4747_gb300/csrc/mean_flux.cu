@@ -726,3 +726,139 @@ lya_status mean_flux_solve_noalloc(const float* tau, int64_t n, double target, d
 }
 
 }  // namespace lya
+
+// ---- building blocks for a root-find split over devices or processes ---------------
+//
+// When the pixels of one request live on several devices, each device reduces
+// its own share and the caller combines the sums (one all-reduce of three
+// numbers per pass) and steps A on the host; these calls are that per-device
+// share.  The single-device root-find above keeps everything on the device.
+namespace lya {
+namespace {
+
+struct SumsOut {
+    double s[3];
+    unsigned int ticket;
+};
+
+// sum tau (compensated), zero count, invalid count.
+__global__ void __launch_bounds__(kThreads) mf_moments_kernel(const float* __restrict__ tau, long long n,
+                                                            Partial* part, SumsOut* out)
+{
+    KahanF32 s;
+    long long z = 0, bad = 0;
+    stream_f32(tau, n, [&](long long, float t) {
+        if (!(t >= 0.f) || !isfinite(t)) { ++bad; return; }
+        s.add(t);
+        z += (t == 0.f);
+    });
+    __shared__ double sh[3][32];
+    double v[3] = {(double)s.value(), (double)z, (double)bad};
+    block_sum<3>(v, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = Partial{v[0], 0.0, 0.0, 0.0, (long long)v[1], (long long)v[2]};
+    if (!last_block(&out->ticket)) return;
+    double tot[3];
+    partial_totals<3>(part, gridDim.x, tot, sh, [](const Partial& p, double (&x)[3]) {
+        x[0] = p.s0; x[1] = (double)p.z; x[2] = (double)p.bad;
+    });
+    if (threadIdx.x != 0) return;
+    out->s[0] = tot[0];
+    out->s[1] = tot[1];
+    out->s[2] = tot[2];
+    out->ticket = 0;
+}
+
+// sum e, sum tau e, sum tau^2 e with e = exp(-A tau).
+__global__ void __launch_bounds__(kThreads) mf_sums_kernel(const float* __restrict__ tau, long long n, double A,
+                                                         Partial* part, SumsOut* out)
+{
+    float a_hi, a_lo;
+    split_rate(A, a_hi, a_lo);
+    KahanF32 s0;
+    float s0c = 0.f, s1 = 0.f, s2 = 0.f;
+    stream_f32(tau, n, [&](long long, float t) {
+        float e, c;
+        exp_neg(t, a_hi, a_lo, e, c);
+        s0.add(e);
+        s0c += c;
+        const float te = t * e;
+        s1 += te;
+        s2 = fmaf(t, te, s2);
+    });
+    __shared__ double sh[4][32];
+    double v[4] = {(double)s0.value(), (double)s0c, (double)s1, (double)s2};
+    block_sum<4>(v, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = Partial{v[0], v[1], v[2], v[3], 0, 0};
+    if (!last_block(&out->ticket)) return;
+    double tot[4];
+    partial_totals<4>(part, gridDim.x, tot, sh, [](const Partial& p, double (&x)[4]) {
+        x[0] = p.s0; x[1] = p.s0c; x[2] = p.s1; x[3] = p.s2;
+    });
+    if (threadIdx.x != 0) return;
+    out->s[0] = tot[0] + tot[1];
+    out->s[1] = tot[2];
+    out->s[2] = tot[3];
+    out->ticket = 0;
+}
+
+__global__ void __launch_bounds__(kThreads) mf_flux_at_kernel(const float* __restrict__ tau, long long n,
+                                                            double A, float* __restrict__ F)
+{
+    float a_hi, a_lo;
+    split_rate(A, a_hi, a_lo);
+    stream_f32(tau, n, [&](long long i, float t) {
+        float e, c;
+        exp_neg(t, a_hi, a_lo, e, c);
+        F[i] = e + c;
+    });
+}
+
+template <typename Launch>
+lya_status run_sums(int64_t n, double* out3, cudaStream_t stream, Launch launch)
+{
+    const int grid = grid_for(n);
+    Partial* part = nullptr;
+    SumsOut* d = nullptr;
+    SumsOut h{};
+    cudaError_t e = cudaMallocAsync((void**)&part, sizeof(Partial) * grid, stream);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&d, sizeof(SumsOut), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, sizeof(SumsOut), stream);
+    if (e == cudaSuccess) {
+        launch(grid, part, d);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(SumsOut), cudaMemcpyDeviceToHost, stream);
+    if (part) cudaFreeAsync(part, stream);
+    if (d) cudaFreeAsync(d, stream);
+    const cudaError_t e2 = cudaStreamSynchronize(stream);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LYA_ENOMEM : LYA_ECUDA;
+    for (int k = 0; k < 3; ++k) out3[k] = h.s[k];
+    return LYA_OK;
+}
+
+}  // namespace
+
+lya_status tau_moments_run(const float* tau, int64_t n, double* out3, cudaStream_t stream)
+{
+    return run_sums(n, out3, stream, [&](int grid, Partial* part, SumsOut* d) {
+        mf_moments_kernel<<<grid, kThreads, 0, stream>>>(tau, n, part, d);
+    });
+}
+
+lya_status mean_flux_sums_run(const float* tau, int64_t n, double A, double* out3, cudaStream_t stream)
+{
+    return run_sums(n, out3, stream, [&](int grid, Partial* part, SumsOut* d) {
+        mf_sums_kernel<<<grid, kThreads, 0, stream>>>(tau, n, A, part, d);
+    });
+}
+
+lya_status flux_at_run(const float* tau, int64_t n, double A, float* flux, cudaStream_t stream)
+{
+    mf_flux_at_kernel<<<grid_for(n), kThreads, 0, stream>>>(tau, n, A, flux);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? LYA_OK : LYA_ECUDA;
+}
+
+}  // namespace lya

@@ -344,3 +344,35 @@ def test_precision_study_1024_skewers(lya, orc, gpc_field, capsys):
         print(f"{'variant':18s} {'max tau rel':>12s} {'max |dF|':>10s} {'max col rel':>12s} {'A/A_o - 1':>11s}")
         for name, rel, dF, dcol, dA in rows:
             print(f"{name:18s} {rel:12.3e} {dF:10.3e} {dcol:12.3e} {dA:11.3e}")
+
+
+def test_split_root_find_matches_single_device(lya, orc):
+    """The per-device shares (lya_tau_moments, lya_mean_flux_sums, lya_flux_at)
+    driven by the split root-find reproduce the single-device root-find; two
+    halves of the pixels combined by summing their shares give the same A."""
+    import torch
+    spec = ls.TINY_20MPC
+    rho, v, t = ls.skewers(spec, np.arange(ls.TINY_20MPC_SKEWERS))
+    field = make_field(lya, spec, rho, v, t)
+    tau = lya.extract_skewers(field, lya.ExtractParams()).ravel()
+    A_ref, F_ref = lya.rescale_mean_flux(tau, ls.TINY_20MPC_FT)
+    A1, _ = lya.rescale_mean_flux_distributed(tau, ls.TINY_20MPC_FT, allreduce=lambda x: list(x))
+    assert A1 == pytest.approx(A_ref, rel=1e-9)
+    halves = [tau[: tau.numel() // 2], tau[tau.numel() // 2:]]
+
+    def allreduce_pair(_):
+        raise AssertionError("unused")
+
+    # emulate two parts in one process: shares summed by hand
+    def moments():
+        return [sum(x) for x in zip(*(lya.tau_moments(h) for h in halves))]
+
+    def sums(A):
+        return [sum(x) for x in zip(*(lya.mean_flux_sums(h, A) for h in halves))]
+
+    A2, _ = lya.rescale_mean_flux_distributed(None, ls.TINY_20MPC_FT, n=tau.numel(), allreduce=lambda x: list(x),
+                                              moments=moments, sums=sums)
+    assert A2 == pytest.approx(A_ref, rel=1e-9)
+    F = torch.cat([lya.flux_at(h, A2) for h in halves])
+    torch.cuda.synchronize()
+    assert float((F - F_ref).abs().max()) <= 1e-6
