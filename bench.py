@@ -222,6 +222,119 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# the served form: Poisson arrivals into the library's serving loop
+# ---------------------------------------------------------------------------
+SERVE_BUDGET = 120 << 30                 # HBM budget of admitted requests (tau + F)
+
+
+def serving_pool(lya, torch, boxes_per_length=4, pool_rows=256):
+    """The resident field pool (density and velocity), built on the device."""
+    specs = ls.serve_field_specs(boxes_per_length)
+    fields = []
+    for sp in specs:
+        rho, v, _ = ls.grid_on_device(sp, ls.SERVE_SKEWERS_PER_FIELD, torch, pool=pool_rows, with_temp=False)
+        fields.append(lya.Field(rho, v, None, box=sp.box, z=sp.z, borrow=True))
+    return specs, fields
+
+
+def serve_stream(lya, srv, fields, reqs, t_end):
+    """Submit ``reqs`` at their arrival times (until t_end s) from one thread,
+    wait for and release each from another; returns [(request, result)], the
+    submitter's lateness (s) per request and the stream's start (ns)."""
+    import queue
+    q = queue.Queue()
+    done, lag = [], []
+    t0 = time.monotonic() + 0.05
+
+    def submitter():
+        for r in reqs:
+            if r.t_arrival > t_end:
+                break
+            dt = t0 + r.t_arrival - time.monotonic()
+            if dt > 0:
+                time.sleep(dt)
+            lag.append(time.monotonic() - (t0 + r.t_arrival))
+            tk = srv.submit(fields[r.field], lya.ExtractParams(t_mode=1, T0=r.T0, gamma=r.gamma), r.ids, r.target)
+            q.put((r, tk))
+        q.put(None)
+
+    def reaper():
+        while True:
+            item = q.get()
+            if item is None:
+                return
+            r, tk = item
+            res = srv.wait(tk, 600.0)
+            done.append((r, res))
+            srv.release(tk)
+
+    th = [threading.Thread(target=submitter), threading.Thread(target=reaper)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    return done, lag, int(t0 * 1e9)
+
+
+def run_serving(lya, torch, warm_s, measure_s, burst=400):
+    """p50/p99 latency and served pixels/s of the Poisson stream, and the
+    loop's capacity (a burst of requests submitted at once)."""
+    specs, fields = serving_pool(lya, torch)
+    reqs = ls.serve_requests(len(fields), int((warm_s + measure_s) * ls.SERVE_RATE * 1.5) + burst)
+    srv = lya.Server(budget_bytes=SERVE_BUDGET, max_slots=256, step_target_us=2000.0)
+    shifts = {}
+    for n in ls.SERVE_N_PIX:
+        k = [i for i, sp in enumerate(specs) if sp.n_pix == n]
+        mid = sorted(k, key=lambda i: specs[i].box)[len(k) // 2]
+        shifts[n] = srv.autotune(fields[mid], lya.ExtractParams(t_mode=1, T0=1.75e4, gamma=1.3), max_rows=1024)
+    info0 = srv.info()
+    launches0 = lya.kernel_launches()
+    done, lag, t0_ns = serve_stream(lya, srv, fields, reqs, warm_s + measure_s)
+    launches = lya.kernel_launches() - launches0
+    info1 = srv.info()
+    w0, w1 = t0_ns + int(warm_s * 1e9), t0_ns + int((warm_s + measure_s) * 1e9)
+    lat, px_done, px_offered, n_meas, failed = [], 0, 0, 0, 0
+    for r, res in done:
+        px = r.ids.size * specs[r.field].n_pix
+        if res.status != 0:
+            failed += 1
+        if warm_s <= r.t_arrival < warm_s + measure_s:
+            lat.append((res.t_done_ns - res.t_submit_ns) * 1e-6)
+            px_offered += px
+            n_meas += 1
+        if w0 <= res.t_done_ns < w1:
+            px_done += px
+    lat = np.array(lat)
+    # capacity: a burst of the next requests, all submitted at once
+    tail = reqs[len(done):len(done) + burst]
+    t_b0 = time.monotonic_ns()
+    tickets = [srv.submit(fields[r.field], lya.ExtractParams(t_mode=1, T0=r.T0, gamma=r.gamma), r.ids, r.target)
+               for r in tail]
+    last, px_b = 0, 0
+    for r, tk in zip(tail, tickets):
+        res = srv.wait(tk, 600.0)
+        last = max(last, res.t_done_ns)
+        px_b += r.ids.size * specs[r.field].n_pix
+        srv.release(tk)
+    cap = px_b / ((last - t_b0) * 1e-9)
+    srv.close()
+    for f in fields:
+        f.close()
+    return {"workload": f"poisson_{ls.SERVE_RATE:g}rps_pool{len(fields)}x{ls.SERVE_SKEWERS_PER_FIELD}",
+            "rate_rps": ls.SERVE_RATE, "warmup_s": warm_s, "measure_s": measure_s, "requests": n_meas,
+            "failed": failed, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+            "served_px_per_s": px_done / measure_s, "offered_px_per_s": px_offered / measure_s,
+            "capacity_px_per_s": cap, "capacity_burst_requests": len(tail),
+            "submit_lag_p99_ms": float(np.percentile(np.array(lag), 99) * 1e3),
+            "steps": info1["steps"] - info0["steps"], "gpu_launches": launches,
+            "group_shift_by_n_pix": {str(k): v for k, v in shifts.items()},
+            "budget_bytes": SERVE_BUDGET, "latency": "submit to result (native steady clock)",
+            "data": "synthetic pool: boxes log-uniform 50-1000 h^-1 Mpc, n_pix 512-8192, T from each request's "
+                    "power law"}
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
@@ -332,6 +445,12 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not grid:
         cpu = oracle_timing(spec, args.cpu_seconds)
 
+    serving = None
+    if not grid and not args.no_serving:
+        del tau, F
+        torch.cuda.empty_cache()
+        serving = run_serving(lya, torch, 2.0, args.serve_seconds)
+
     if rank == 0:
         line = {"metric": METRIC, "value": world * n_px / (ms / 1e3), "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -339,12 +458,36 @@ def run_ours(args):
                 "config": workload_config(spec, S, {"parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                                                     "A": A, "mean_flux": st.mean_flux}, grid),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk}
+                "clocks": clk, "serving": serving}
         print(json.dumps(line), flush=True)
     field.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+    return 0
+
+
+
+def run_serving_workload(args):
+    """The served form alone: p50/p99 latency and served pixels/s."""
+    import torch
+    world, rank, local = dist_setup()
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1105_4747_gb300 as lya
+    clocks = ClockSampler(local)
+    clocks.start()
+    sv = run_serving(lya, torch, 5.0, 60.0)
+    clk = clocks.stop()
+    if rank == 0:
+        line = {"metric": "served tau-skewer pixels/s, Poisson 200 req/s; p50/p99 latency", "value":
+                sv["served_px_per_s"] * world, "unit": UNIT, "n_gpus": world, "steps": sv["steps"], "warmup": 5,
+                "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic", "config": {"workload": sv["workload"],
+                                                               "parallelism": "replicas" if world > 1 else "1 GPU"},
+                "latency_ms": {"p50": sv["p50_ms"], "p99": sv["p99_ms"]}, "serving": sv,
+                "gpu_launches": sv["gpu_launches"], "clocks": clk}
+        print(json.dumps(line), flush=True)
     return 0
 
 
@@ -355,14 +498,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--skewers", type=int, default=None, help="fewer skewers (debug only)")
-    ap.add_argument("--workload", choices=["gpc", "grid1536"], default="gpc",
-                    help="gpc: 65,536 x 4,096 px (the metric's workload); grid1536: all rows of a 1536^3 grid")
+    ap.add_argument("--workload", choices=["gpc", "grid1536", "serving"], default="gpc",
+                    help="gpc: 65,536 x 4,096 px (the metric's workload); grid1536: all rows of a 1536^3 grid; "
+                         "serving: 60 s of Poisson requests after 5 s of warm-up")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="measured seconds of the Poisson request stream in the default run")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serving":
+        return run_serving_workload(args)
     return run_ours(args)
 
 

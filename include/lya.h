@@ -47,7 +47,9 @@ typedef enum {
     LYA_ENOCONV = -4,    /* the mean-flux root-find did not converge / no root */
     LYA_ETIMEDOUT = -5,  /* a bounded device wait gave up                     */
     LYA_EBUDGET = -6,    /* a request does not fit the memory budget          */
-    LYA_EDEVICE = -7     /* no usable sm_103 device                           */
+    LYA_EDEVICE = -7,    /* no usable sm_103 device                           */
+    LYA_EBUSY = -8       /* object in use (field held by a server request, or  */
+                         /* a server call that needs an idle server)          */
 } lya_status;
 
 /* Opaque handle to a field resident in device memory. */
@@ -210,6 +212,104 @@ lya_status lya_flux_at(const float* tau, int64_t n, double A, float* flux_out, v
  */
 lya_status lya_flux_stats(const float* flux, int64_t n, lya_flux_stats_t* out,
                           void* stream);
+
+/* ======================================================================
+ * Serving: a persistent request loop over resident fields.
+ *
+ * The paper has no serving layer; this is the library's front end for many
+ * independent extraction requests, each an instance of Eq. 4-6 plus its own
+ * mean-flux normalisation (Sec. 2.3).  A server owns a worker thread, a CUDA
+ * stream, one device arena of hbm_budget_bytes and a CUDA graph of one step:
+ *   - the optical-depth kernel, persistent (one 1024-thread CTA per SM),
+ *     over the step's work list: each CTA takes tasks of up to 8 skewers of
+ *     one request, split over 1, 2, 4 or 8 warp groups (the group shape of
+ *     each skewer length is chosen by lya_server_autotune);
+ *   - the mean-flux root-find of every request whose skewers are complete,
+ *     all requests in the same passes (init, then two rounds of two Halley
+ *     passes and one flux pass that writes F and its statistics).
+ * Each step the worker admits queued requests in arrival order while a slot
+ * and arena memory are free, plans the step (a request's skewers may be
+ * spread over several steps so that short requests do not wait behind long
+ * ones), copies the plan to the device, launches the graph and reads back
+ * the finished requests.  Requests that arrive while a step runs join the
+ * next one.
+ *
+ * A request holds 8 bytes per pixel of arena memory (tau and F) and one slot
+ * until its root-find ends; then tau is freed and F stays until
+ * lya_server_release.  The field must outlive the request: lya_destroy_field
+ * returns LYA_EBUSY while a request on it is unfinished.
+ * ====================================================================== */
+typedef struct lya_server_s* lya_server;
+
+typedef struct {
+    size_t hbm_budget_bytes; /* arena size: tau and F of admitted requests       */
+    int max_slots;           /* requests in flight at once (1..4096)             */
+    double step_target_us;   /* estimated optical-depth work per step, us (> 0)  */
+    double tol;              /* root-find tolerance on <F> (> 0; e.g. 1e-12)     */
+    int max_iter;            /* root-find pass limit (>= 1; e.g. 50)             */
+} lya_server_config;
+
+typedef struct {
+    int done;                /* 1 when the request has finished                  */
+    lya_status status;       /* LYA_OK, or why it failed (valid when done)       */
+    double A;                /* the request's mean-flux constant                  */
+    int iterations;          /* root-find passes that updated A                  */
+    lya_flux_stats_t stats;  /* statistics of the request's F                    */
+    const float* flux;       /* device [n_ids][n_pix] F, owned by the server     */
+                             /* until lya_server_release; NULL if failed         */
+    int64_t n_ids, n_pix;
+    uint64_t t_submit_ns, t_admit_ns, t_done_ns;  /* steady-clock stamps         */
+} lya_server_result;
+
+typedef struct {
+    uint64_t steps;          /* graph launches so far                            */
+    uint64_t submitted, completed, failed;
+    size_t arena_used, arena_peak, arena_capacity;
+    int slots_in_use, queued;
+    int group_shift[14];     /* tuned log2(skewers per CTA) for n_pix = 2^k;    */
+                             /* -1 where not tuned (a default is used)          */
+} lya_server_info_t;
+
+/* Creates a server on the current device.  LYA_ENOMEM if the arena cannot be
+ * allocated. */
+lya_status lya_server_create(const lya_server_config* cfg, lya_server* out);
+
+/*
+ * Times the optical-depth kernel of the server on up to max_rows skewers of
+ * `field` with `params` for every group shape that fits the field's skewer
+ * length, and keeps the fastest for that length.  The server must be idle
+ * (LYA_EBUSY otherwise).  *shift_out (nullable) gets log2(skewers per CTA).
+ */
+lya_status lya_server_autotune(lya_server srv, lya_field field, const lya_extract_params* params,
+                               int64_t max_rows, int* shift_out);
+
+/*
+ * Queues one request: skewers ids[0..n_ids) (host array, copied) of `field`
+ * extracted with `params` (F32 precisions only), then A solved so that the
+ * mean of exp(-A tau) over all its pixels is target_mean_flux.  Returns
+ * LYA_EBUDGET if the request alone exceeds the arena, LYA_EINVAL for a bad
+ * argument or an id out of range, LYA_ECUDA if the server has failed.
+ */
+lya_status lya_server_submit(lya_server srv, lya_field field, const lya_extract_params* params,
+                             const int64_t* ids, int64_t n_ids, double target_mean_flux,
+                             uint64_t* ticket);
+
+/* Current state of a request (never blocks). LYA_EINVAL for an unknown ticket. */
+lya_status lya_server_poll(lya_server srv, uint64_t ticket, lya_server_result* out);
+
+/* Waits until the request is done or timeout_s passes (LYA_ETIMEDOUT). */
+lya_status lya_server_wait(lya_server srv, uint64_t ticket, double timeout_s, lya_server_result* out);
+
+/* Copies a finished request's F (n_ids * n_pix floats) to dst (device) on stream. */
+lya_status lya_server_copy_flux(lya_server srv, uint64_t ticket, float* dst, void* stream);
+
+/* Frees a finished request's F and forgets the ticket (LYA_EBUSY if unfinished). */
+lya_status lya_server_release(lya_server srv, uint64_t ticket);
+
+lya_status lya_server_info(lya_server srv, lya_server_info_t* out);
+
+/* Stops the worker (unfinished requests fail with LYA_ECUDA), frees everything. */
+lya_status lya_server_destroy(lya_server srv);
 
 /* Human-readable text of a status code (static storage). */
 const char* lya_strerror(lya_status status);

@@ -220,3 +220,57 @@ def grid_on_device(spec: FieldSpec, n_rows: int, torch, device="cuda", pool: int
             dst[lo:lo + rows.numel()] = torch.gather(src[base], 1, idx)
     del pools
     return tuple(outs) + ((None,) if not with_temp else ())
+
+
+# ---- a served request stream --------------------------------------------------------
+# A pool of resident fields (density and velocity only; the temperature comes
+# from each request's own power law): boxes log-uniform in [50, 1000] h^-1 Mpc,
+# skewer lengths from {512, ..., 8192}, the paper-scale field recipe (k_J = 4,
+# sigma_delta = 1.5, z = 2.5).  Requests arrive as a Poisson stream; each names
+# a field of the pool, a log-uniform number of its skewers, its own T0, gamma
+# and target mean flux.
+SERVE_N_PIX = (512, 1024, 2048, 4096, 8192)
+SERVE_BOX_RANGE = (50.0, 1000.0)
+SERVE_SKEWERS_PER_FIELD = 4096
+SERVE_RATE = 200.0                 # requests per second
+SERVE_SEED = 3
+
+
+@dataclass(frozen=True)
+class ServeRequest:
+    t_arrival: float               # seconds after the stream starts
+    field: int                     # index into the pool
+    ids: np.ndarray                # skewer ids of the field
+    T0: float
+    gamma: float
+    target: float                  # mean flux the request is rescaled to
+
+
+def serve_field_specs(boxes_per_length: int = 4, seed: int = SERVE_SEED) -> list:
+    """The pool: ``boxes_per_length`` fields for every skewer length."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0]))
+    lo, hi = np.log(SERVE_BOX_RANGE[0]), np.log(SERVE_BOX_RANGE[1])
+    specs = []
+    for n in SERVE_N_PIX:
+        for b in range(boxes_per_length):
+            box = float(np.exp(rng.uniform(lo, hi)))
+            specs.append(FieldSpec(n_pix=n, box=box, z=2.5, k_j=4.0, sigma_delta=1.5, T0=1.5e4, gamma=1.5,
+                                   seed=seed * 1000 + len(specs)))
+    return specs
+
+
+def serve_requests(n_fields: int, count: int, rate: float = SERVE_RATE, seed: int = SERVE_SEED,
+                   skewers_per_field: int = SERVE_SKEWERS_PER_FIELD, max_skewers: int = 4096) -> list:
+    """``count`` requests of a Poisson stream at ``rate`` per second."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 1]))
+    t = 0.0
+    out = []
+    top = min(max_skewers, skewers_per_field)
+    for _ in range(count):
+        t += float(rng.exponential(1.0 / rate))
+        f = int(rng.integers(n_fields))
+        n = int(np.clip(np.round(np.exp(rng.uniform(0.0, np.log(top)))), 1, top))
+        ids = np.sort(rng.choice(skewers_per_field, size=n, replace=False)).astype(np.int64)
+        out.append(ServeRequest(t, f, ids, float(rng.uniform(1.0e4, 2.5e4)), float(rng.uniform(1.0, 1.6)),
+                                float(rng.uniform(0.65, 0.85))))
+    return out

@@ -16,6 +16,8 @@ from ._binding import (  # noqa: F401
     Field,
     FluxStats,
     LyaError,
+    Server,
+    ServerResult,
     extract_skewers,
     flux_at,
     flux_stats,

@@ -20,8 +20,8 @@ _LIB_PATH = os.path.join(_HERE, "_build", "liblya.so")
 _lock = threading.Lock()
 _lib = None
 
-LYA_OK, LYA_EINVAL, LYA_ENOMEM, LYA_ECUDA, LYA_ENOCONV, LYA_ETIMEDOUT, LYA_EBUDGET, LYA_EDEVICE = \
-    0, -1, -2, -3, -4, -5, -6, -7
+LYA_OK, LYA_EINVAL, LYA_ENOMEM, LYA_ECUDA, LYA_ENOCONV, LYA_ETIMEDOUT, LYA_EBUDGET, LYA_EDEVICE, LYA_EBUSY = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8
 SRC_HOST, SRC_DEVICE_COPY, SRC_DEVICE_BORROW = 0, 1, 2
 PREC_F32_COMPENSATED, PREC_F32_NAIVE, PREC_F64 = 0, 1, 2
 
@@ -52,6 +52,25 @@ class _ExtractParams(ctypes.Structure):
 class _FluxStats(ctypes.Structure):
     _fields_ = [("mean_flux", ctypes.c_double), ("var_flux", ctypes.c_double),
                 ("tau_eff", ctypes.c_double), ("pdf", ctypes.c_int64 * 21), ("n", ctypes.c_int64)]
+
+
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int),
+                ("step_target_us", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int)]
+
+
+class _ServerResult(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int), ("status", ctypes.c_int), ("A", ctypes.c_double),
+                ("iterations", ctypes.c_int), ("stats", _FluxStats), ("flux", ctypes.c_void_p),
+                ("n_ids", ctypes.c_int64), ("n_pix", ctypes.c_int64), ("t_submit_ns", ctypes.c_uint64),
+                ("t_admit_ns", ctypes.c_uint64), ("t_done_ns", ctypes.c_uint64)]
+
+
+class _ServerInfo(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_uint64), ("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("arena_used", ctypes.c_size_t), ("arena_peak", ctypes.c_size_t),
+                ("arena_capacity", ctypes.c_size_t), ("slots_in_use", ctypes.c_int), ("queued", ctypes.c_int),
+                ("group_shift", ctypes.c_int * 14)]
 
 
 def kernel_launches() -> int:
@@ -92,10 +111,22 @@ def load_library():
         lib.lya_tau_moments.argtypes = [vp, i64, ctypes.POINTER(d), vp]
         lib.lya_mean_flux_sums.argtypes = [vp, i64, d, ctypes.POINTER(d), vp]
         lib.lya_flux_at.argtypes = [vp, i64, d, vp, vp]
+        u64 = ctypes.c_uint64
+        lib.lya_server_create.argtypes = [ctypes.POINTER(_ServerConfig), ctypes.POINTER(vp)]
+        lib.lya_server_autotune.argtypes = [vp, vp, ctypes.POINTER(_ExtractParams), i64, ctypes.POINTER(i32)]
+        lib.lya_server_submit.argtypes = [vp, vp, ctypes.POINTER(_ExtractParams), vp, i64, d, ctypes.POINTER(u64)]
+        lib.lya_server_poll.argtypes = [vp, u64, ctypes.POINTER(_ServerResult)]
+        lib.lya_server_wait.argtypes = [vp, u64, d, ctypes.POINTER(_ServerResult)]
+        lib.lya_server_copy_flux.argtypes = [vp, u64, vp, vp]
+        lib.lya_server_release.argtypes = [vp, u64]
+        lib.lya_server_info.argtypes = [vp, ctypes.POINTER(_ServerInfo)]
+        lib.lya_server_destroy.argtypes = [vp]
         for name in ("lya_create_field", "lya_field_load", "lya_destroy_field", "lya_field_status",
                      "lya_field_shape", "lya_extract_skewers", "lya_rescale_mean_flux",
                      "lya_rescale_mean_flux_noalloc", "lya_flux_stats", "lya_tau_moments",
-                     "lya_mean_flux_sums", "lya_flux_at"):
+                     "lya_mean_flux_sums", "lya_flux_at", "lya_server_create", "lya_server_autotune",
+                     "lya_server_submit", "lya_server_poll", "lya_server_wait", "lya_server_copy_flux",
+                     "lya_server_release", "lya_server_info", "lya_server_destroy"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -337,3 +368,121 @@ def flux_stats(flux, stream=None) -> FluxStats:
     _check(load_library().lya_flux_stats(flux.data_ptr(), flux.numel(), ctypes.byref(out),
                                          _stream_handle(stream)), "lya_flux_stats")
     return FluxStats(out.mean_flux, out.var_flux, out.tau_eff, np.array(out.pdf[:], dtype=np.int64), out.n)
+
+
+@dataclass
+class ServerResult:
+    """State of one served request (lya_server_result)."""
+    done: bool
+    status: int
+    A: float
+    iterations: int
+    stats: FluxStats
+    n_ids: int
+    n_pix: int
+    t_submit_ns: int
+    t_admit_ns: int
+    t_done_ns: int
+    flux_ptr: int
+
+    @property
+    def latency_s(self) -> float:
+        return (self.t_done_ns - self.t_submit_ns) * 1e-9 if self.done else math.nan
+
+
+class Server:
+    """The serving loop (lya_server_*): requests are queued with ``submit``,
+    admitted by memory budget and run in steps by the library's worker thread.
+
+    ``budget_bytes`` bounds tau + F of admitted requests (8 bytes per pixel);
+    ``max_slots`` the requests in flight; ``step_target_us`` the optical-depth
+    work packed into one step.
+    """
+
+    def __init__(self, budget_bytes: int, max_slots: int = 256, step_target_us: float = 2000.0,
+                 tol: float = 1e-12, max_iter: int = 50):
+        lib = load_library()
+        self._handle = None
+        cfg = _ServerConfig(int(budget_bytes), int(max_slots), float(step_target_us), float(tol), int(max_iter))
+        out = ctypes.c_void_p()
+        _check(lib.lya_server_create(ctypes.byref(cfg), ctypes.byref(out)), "lya_server_create")
+        self._handle = out
+        self._fields = {}                # keep fields of unfinished requests alive
+
+    def autotune(self, field: Field, params: ExtractParams, max_rows: int = 1024) -> int:
+        """Choose the group shape for this field's skewer length; returns log2(skewers per CTA)."""
+        shift = ctypes.c_int(-1)
+        p = params._c()
+        _check(load_library().lya_server_autotune(self._handle, field.handle, ctypes.byref(p), int(max_rows),
+                                                  ctypes.byref(shift)), "lya_server_autotune")
+        return shift.value
+
+    def submit(self, field: Field, params: ExtractParams, ids, target_mean_flux: float) -> int:
+        ids_h = np.ascontiguousarray(np.asarray(ids, dtype=np.int64).ravel())
+        ticket = ctypes.c_uint64()
+        p = params._c()
+        _check(load_library().lya_server_submit(self._handle, field.handle, ctypes.byref(p), ids_h.ctypes.data,
+                                                ids_h.size, float(target_mean_flux), ctypes.byref(ticket)),
+               "lya_server_submit")
+        self._fields[ticket.value] = field
+        return ticket.value
+
+    @staticmethod
+    def _result(r: _ServerResult) -> ServerResult:
+        st = FluxStats(r.stats.mean_flux, r.stats.var_flux, r.stats.tau_eff,
+                       np.array(r.stats.pdf[:], dtype=np.int64), r.stats.n)
+        return ServerResult(bool(r.done), int(r.status), r.A, int(r.iterations), st, int(r.n_ids), int(r.n_pix),
+                            int(r.t_submit_ns), int(r.t_admit_ns), int(r.t_done_ns), int(r.flux or 0))
+
+    def poll(self, ticket: int) -> ServerResult:
+        r = _ServerResult()
+        _check(load_library().lya_server_poll(self._handle, int(ticket), ctypes.byref(r)), "lya_server_poll")
+        return self._result(r)
+
+    def wait(self, ticket: int, timeout_s: float = 60.0) -> ServerResult:
+        r = _ServerResult()
+        _check(load_library().lya_server_wait(self._handle, int(ticket), float(timeout_s), ctypes.byref(r)),
+               "lya_server_wait")
+        return self._result(r)
+
+    def flux(self, ticket: int, out=None, stream=None):
+        """A copy of a finished request's F as a CUDA tensor [n_ids][n_pix]."""
+        torch = _torch()
+        r = self.poll(ticket)
+        if out is None:
+            out = torch.empty((r.n_ids, r.n_pix), dtype=torch.float32, device="cuda")
+        _require_cuda_f32(out, "out")
+        if out.numel() != r.n_ids * r.n_pix:
+            raise ValueError("out has the wrong size")
+        _check(load_library().lya_server_copy_flux(self._handle, int(ticket), out.data_ptr(),
+                                                   _stream_handle(stream)), "lya_server_copy_flux")
+        return out
+
+    def release(self, ticket: int):
+        _check(load_library().lya_server_release(self._handle, int(ticket)), "lya_server_release")
+        self._fields.pop(int(ticket), None)
+
+    def info(self) -> dict:
+        i = _ServerInfo()
+        _check(load_library().lya_server_info(self._handle, ctypes.byref(i)), "lya_server_info")
+        return {"steps": i.steps, "submitted": i.submitted, "completed": i.completed, "failed": i.failed,
+                "arena_used": i.arena_used, "arena_peak": i.arena_peak, "arena_capacity": i.arena_capacity,
+                "slots_in_use": i.slots_in_use, "queued": i.queued, "group_shift": list(i.group_shift)}
+
+    def close(self):
+        if self._handle:
+            load_library().lya_server_destroy(self._handle)
+            self._handle = None
+            self._fields.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -81,19 +81,6 @@ void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_r
 uint64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace lya
 
-struct lya_field_s {
-    lya_field_desc desc;
-    float* rho = nullptr;
-    float* vpec = nullptr;
-    float* temp = nullptr;
-    bool owned = false;
-    int* d_err = nullptr;            // device error word of extract launches
-    lya::FieldCheck* d_check = nullptr;
-    float temp_max = 0.f;            // largest T where rho > 0 (stored-T fields)
-    float rho_max = 0.f;             // largest rho
-    float rho_minpos = 0.f;          // smallest rho > 0
-    int device = 0;
-};
 
 namespace {
 
@@ -139,6 +126,80 @@ void release(lya_field f)
 
 }  // namespace
 
+namespace lya {
+
+// Validates the extraction parameters against the field and fills every
+// field- and parameter-dependent member of *out (ids, n_rows and tau_out are
+// left for the caller): the FP64 constants of Eq. 4-6 in both precisions and
+// the window bound w_max from the largest temperature any source can have.
+lya_status make_tau_launch(lya_field f, const lya_extract_params* p, TauLaunch* out)
+{
+    if (!f || !p || !out) return LYA_EINVAL;
+    if (p->t_mode != 0 && p->t_mode != 1) return LYA_EINVAL;
+    if (p->t_mode == 0 && !f->temp) return LYA_EINVAL;
+    if (p->t_mode == 1) {
+        if (!(p->T0 > 0.0) || !std::isfinite(p->T0) || !std::isfinite(p->gamma)) return LYA_EINVAL;
+        if (!(p->delta_pivot > 0.0)) return LYA_EINVAL;
+    }
+    if (!(p->gamma12 > 0.0) || !std::isfinite(p->gamma12)) return LYA_EINVAL;
+    if (!(p->nsigma >= 1.0 && p->nsigma <= 40.0)) return LYA_EINVAL;
+    if (p->precision < LYA_PREC_F32_COMPENSATED || p->precision > LYA_PREC_F64) return LYA_EINVAL;
+    const int N = (int)f->desc.n_pix;
+    const Physics ph = physics(f->desc, p->gamma12);
+    // |v_pec| < c is checked per value; keep |v_pec|/du below 2^29 pixels so the
+    // kernels' target-pixel arithmetic stays in 32-bit integers
+    if (!(ph.du > 2.99792458e5 / 536870912.0)) return LYA_EINVAL;
+
+    // Largest temperature any source can have -> bound on the window half-width
+    // (pixels) of every line: nsigma b(T_max)/du + 1/2 (the residual), +1 margin.
+    double t_max;
+    if (p->t_mode == 0) {
+        t_max = f->temp_max;
+    } else {
+        const double piv = p->delta_pivot;
+        const double r_hi = std::fmin((double)f->rho_max, piv);
+        const double r_lo = std::fmin((double)f->rho_minpos, piv);
+        const double g1 = p->gamma - 1.0;
+        t_max = p->T0 * std::fmax(r_hi > 0 ? std::pow(r_hi, g1) : 0.0, r_lo > 0 ? std::pow(r_lo, g1) : 0.0);
+    }
+    const double b_max = ph.b1e4 * std::sqrt(std::fmax(t_max, 0.0) * 1e-4);
+    double w = std::floor(p->nsigma * b_max / ph.du + 0.5) + 1.0;
+    if (!(w >= 1.0)) w = 1.0;
+    const int w_cap = (N - 1) / 2;
+    const int w_max = w > (double)w_cap ? w_cap : (int)w;
+
+    lya::TauLaunch& L = *out;
+    L = lya::TauLaunch{};
+    L.rho = f->rho;
+    L.vpec = f->vpec;
+    L.temp = p->t_mode == 0 ? f->temp : nullptr;
+    L.n_skewers = f->desc.n_skewers;
+    L.n_pix = N;
+    L.err = f->d_err;
+    L.w_max = w_max;
+    L.t_mode = p->t_mode;
+    L.du_hi = (float)ph.du;
+    L.du_lo = (float)(ph.du - (double)L.du_hi);
+    L.inv_du = (float)(1.0 / ph.du);
+    L.c_coef = (float)(std::sqrt(kLog2e) / ph.b1e4);
+    L.h_coef = (float)(p->nsigma * std::sqrt(kLog2e));
+    L.K = (float)ph.K;
+    L.T0 = (float)p->T0;
+    L.gm1 = (float)(p->gamma - 1.0);
+    L.pivot = std::isfinite(p->delta_pivot) ? (float)p->delta_pivot : INFINITY;
+    L.du_d = ph.du;
+    L.inv_du_d = 1.0 / ph.du;
+    L.c_coef_d = std::sqrt(kLog2e) / ph.b1e4;
+    L.h_coef_d = p->nsigma * std::sqrt(kLog2e);
+    L.K_d = ph.K;
+    L.T0_d = p->T0;
+    L.gm1_d = p->gamma - 1.0;
+    L.pivot_d = p->delta_pivot;
+    return LYA_OK;
+}
+
+}  // namespace lya
+
 extern "C" {
 
 const char* lya_strerror(lya_status s)
@@ -152,6 +213,7 @@ const char* lya_strerror(lya_status s)
     case LYA_ETIMEDOUT: return "bounded device wait timed out";
     case LYA_EBUDGET: return "request exceeds the memory budget";
     case LYA_EDEVICE: return "no usable sm_103 CUDA device";
+    case LYA_EBUSY: return "object in use (a server holds requests on the field, or the server is busy)";
     }
     return "unknown status";
 }
@@ -214,6 +276,7 @@ lya_status lya_field_load(lya_field f, const float* rho, const float* vpec, cons
 lya_status lya_destroy_field(lya_field f)
 {
     if (!f) return LYA_EINVAL;
+    if (f->users.load() != 0) return LYA_EBUSY;      // a server still holds requests on it
     cudaError_t e = cudaDeviceSynchronize();
     release(f);
     return from_cuda(e);
@@ -246,69 +309,13 @@ lya_status lya_extract_skewers(lya_field f, const lya_extract_params* p, const i
     if (n_ids < 0 || (n_ids > 0 && !tau_out)) return LYA_EINVAL;
     if (!ids && n_ids != 0 && n_ids != f->desc.n_skewers) return LYA_EINVAL;
     if (n_ids > 0x7fffffffLL) return LYA_EINVAL;
-    if (p->t_mode != 0 && p->t_mode != 1) return LYA_EINVAL;
-    if (p->t_mode == 0 && !f->temp) return LYA_EINVAL;
-    if (p->t_mode == 1) {
-        if (!(p->T0 > 0.0) || !std::isfinite(p->T0) || !std::isfinite(p->gamma)) return LYA_EINVAL;
-        if (!(p->delta_pivot > 0.0)) return LYA_EINVAL;
-    }
-    if (!(p->gamma12 > 0.0) || !std::isfinite(p->gamma12)) return LYA_EINVAL;
-    if (!(p->nsigma >= 1.0 && p->nsigma <= 40.0)) return LYA_EINVAL;
-    if (p->precision < LYA_PREC_F32_COMPENSATED || p->precision > LYA_PREC_F64) return LYA_EINVAL;
-    const int N = (int)f->desc.n_pix;
-    const Physics ph = physics(f->desc, p->gamma12);
-    // |v_pec| < c is checked per value; keep |v_pec|/du below 2^29 pixels so the
-    // kernels' target-pixel arithmetic stays in 32-bit integers
-    if (!(ph.du > 2.99792458e5 / 536870912.0)) return LYA_EINVAL;
-
-    // Largest temperature any source can have -> bound on the window half-width
-    // (pixels) of every line: nsigma b(T_max)/du + 1/2 (the residual), +1 margin.
-    double t_max;
-    if (p->t_mode == 0) {
-        t_max = f->temp_max;
-    } else {
-        const double piv = p->delta_pivot;
-        const double r_hi = std::fmin((double)f->rho_max, piv);
-        const double r_lo = std::fmin((double)f->rho_minpos, piv);
-        const double g1 = p->gamma - 1.0;
-        t_max = p->T0 * std::fmax(r_hi > 0 ? std::pow(r_hi, g1) : 0.0, r_lo > 0 ? std::pow(r_lo, g1) : 0.0);
-    }
-    const double b_max = ph.b1e4 * std::sqrt(std::fmax(t_max, 0.0) * 1e-4);
-    double w = std::floor(p->nsigma * b_max / ph.du + 0.5) + 1.0;
-    if (!(w >= 1.0)) w = 1.0;
-    const int w_cap = (N - 1) / 2;
-    const int w_max = w > (double)w_cap ? w_cap : (int)w;
-    if (lya::tau_smem_bytes(N, w_max, p->precision) > lya::max_dynamic_smem()) return LYA_EINVAL;
-
-    lya::TauLaunch L{};
-    L.rho = f->rho;
-    L.vpec = f->vpec;
-    L.temp = p->t_mode == 0 ? f->temp : nullptr;
+    lya::TauLaunch L;
+    const lya_status st = lya::make_tau_launch(f, p, &L);
+    if (st != LYA_OK) return st;
+    if (lya::tau_smem_bytes(L.n_pix, L.w_max, p->precision) > lya::max_dynamic_smem()) return LYA_EINVAL;
     L.ids = ids;
     L.n_rows = n_ids;
-    L.n_skewers = f->desc.n_skewers;
-    L.n_pix = N;
     L.tau_out = tau_out;
-    L.err = f->d_err;
-    L.w_max = w_max;
-    L.t_mode = p->t_mode;
-    L.du_hi = (float)ph.du;
-    L.du_lo = (float)(ph.du - (double)L.du_hi);
-    L.inv_du = (float)(1.0 / ph.du);
-    L.c_coef = (float)(std::sqrt(kLog2e) / ph.b1e4);
-    L.h_coef = (float)(p->nsigma * std::sqrt(kLog2e));
-    L.K = (float)ph.K;
-    L.T0 = (float)p->T0;
-    L.gm1 = (float)(p->gamma - 1.0);
-    L.pivot = std::isfinite(p->delta_pivot) ? (float)p->delta_pivot : INFINITY;
-    L.du_d = ph.du;
-    L.inv_du_d = 1.0 / ph.du;
-    L.c_coef_d = std::sqrt(kLog2e) / ph.b1e4;
-    L.h_coef_d = p->nsigma * std::sqrt(kLog2e);
-    L.K_d = ph.K;
-    L.T0_d = p->T0;
-    L.gm1_d = p->gamma - 1.0;
-    L.pivot_d = p->delta_pivot;
     return from_cuda(lya::launch_tau(L, p->precision, static_cast<cudaStream_t>(stream)));
 }
 

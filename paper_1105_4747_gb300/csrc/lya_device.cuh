@@ -65,13 +65,32 @@ __device__ __forceinline__ int warp_inclusive_scan(int v)
     return v;
 }
 
+// A run of consecutive warps of the block that works on one skewer: threads
+// [base, base + nt) with nt a multiple of 32 and base a multiple of 32, so
+// lane numbers match the hardware's.  The whole block is the group with
+// barrier 0 (__syncthreads); smaller groups synchronise on their own named
+// barrier (PTX bar.sync id, nt).
+struct Group {
+    int tid;     // thread index within the group
+    int nt;      // threads in the group
+    int bar;     // 0: whole block; 1..15: named barrier of this group
+    __device__ __forceinline__ void sync() const
+    {
+        if (bar == 0) __syncthreads();
+        else asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nt) : "memory");
+    }
+};
+
+__device__ __forceinline__ Group whole_block() { return Group{(int)threadIdx.x, (int)blockDim.x, 0}; }
+
 // In-place exclusive scan of data[0..n) (ints in shared memory) by the
-// whole block; returns the total on every thread.  warp_tot holds >= 32
-// ints of shared scratch.  Contains __syncthreads(): call from all threads.
-__device__ inline int block_exclusive_scan(int* data, int n, int* warp_tot)
+// group; returns the total on every thread.  warp_tot holds >= 33 ints of
+// shared scratch private to the group.  Synchronises the group: call from
+// all of its threads.
+__device__ inline int block_exclusive_scan(int* data, int n, int* warp_tot, const Group& g)
 {
-    const int nt = blockDim.x;
-    const int tid = threadIdx.x;
+    const int nt = g.nt;
+    const int tid = g.tid;
     const int per = (n + nt - 1) / nt;
     const int lo = min(n, tid * per), hi = min(n, lo + per);
     int local = 0;
@@ -79,14 +98,14 @@ __device__ inline int block_exclusive_scan(int* data, int n, int* warp_tot)
     int inc = warp_inclusive_scan(local);
     const int warp = tid >> 5, lane = tid & 31, nwarps = (nt + 31) >> 5;
     if (lane == 31) warp_tot[warp] = inc;
-    __syncthreads();
+    g.sync();
     if (warp == 0) {
         int w = lane < nwarps ? warp_tot[lane] : 0;
         int wi = warp_inclusive_scan(w);
         if (lane < nwarps) warp_tot[lane] = wi - w;     // exclusive warp offsets
         if (lane == 31) warp_tot[32] = wi;              // total
     }
-    __syncthreads();
+    g.sync();
     int run = warp_tot[warp] + inc - local;
     for (int k = lo; k < hi; ++k) {
         int c = data[k];
@@ -94,8 +113,13 @@ __device__ inline int block_exclusive_scan(int* data, int n, int* warp_tot)
         run += c;
     }
     int total = warp_tot[32];
-    __syncthreads();
+    g.sync();
     return total;
+}
+
+__device__ inline int block_exclusive_scan(int* data, int n, int* warp_tot)
+{
+    return block_exclusive_scan(data, n, warp_tot, whole_block());
 }
 
 // Inclusive warp scan with max (ascending lanes) or min (descending lanes).
@@ -120,11 +144,12 @@ __device__ __forceinline__ int warp_suffix_min(int v)
     return v;
 }
 
-// In-place inclusive prefix max of data[0..n) by the whole block.
-// warp_tmp holds >= 32 ints of shared scratch.  Contains __syncthreads().
-__device__ inline void block_prefix_max(int* data, int n, int* warp_tmp, int lowest)
+// In-place inclusive prefix max of data[0..n) by the group.
+// warp_tmp holds >= 32 ints of the group's shared scratch.  Ends with a
+// group barrier.
+__device__ inline void block_prefix_max(int* data, int n, int* warp_tmp, int lowest, const Group& g)
 {
-    const int nt = blockDim.x, tid = threadIdx.x;
+    const int nt = g.nt, tid = g.tid;
     const int per = (n + nt - 1) / nt;
     const int lo = min(n, tid * per), hi = min(n, lo + per);
     int local = lowest;
@@ -132,27 +157,28 @@ __device__ inline void block_prefix_max(int* data, int n, int* warp_tmp, int low
     const int warp = tid >> 5, lane = tid & 31, nwarps = (nt + 31) >> 5;
     int inc = warp_scan_max(local);
     if (lane == 31) warp_tmp[warp] = inc;
-    __syncthreads();
+    g.sync();
     if (warp == 0) {
         int w = lane < nwarps ? warp_tmp[lane] : lowest;
         int wi = warp_scan_max(w);
         int ex = __shfl_up_sync(0xffffffffu, wi, 1);
         if (lane < nwarps) warp_tmp[lane] = lane ? ex : lowest;   // max over earlier warps
     }
-    __syncthreads();
+    g.sync();
     int ex_thread = __shfl_up_sync(0xffffffffu, inc, 1);
     int run = max(warp_tmp[warp], lane ? ex_thread : lowest);
     for (int k = lo; k < hi; ++k) {
         run = max(run, data[k]);
         data[k] = run;
     }
-    __syncthreads();
+    g.sync();
 }
 
-// In-place inclusive suffix min of data[0..n) (data[k] = min data[k..n)).
-__device__ inline void block_suffix_min(int* data, int n, int* warp_tmp, int highest)
+// In-place inclusive suffix min of data[0..n) (data[k] = min data[k..n)) by
+// the group.  Ends with a group barrier.
+__device__ inline void block_suffix_min(int* data, int n, int* warp_tmp, int highest, const Group& g)
 {
-    const int nt = blockDim.x, tid = threadIdx.x;
+    const int nt = g.nt, tid = g.tid;
     const int per = (n + nt - 1) / nt;
     const int lo = min(n, tid * per), hi = min(n, lo + per);
     int local = highest;
@@ -160,21 +186,21 @@ __device__ inline void block_suffix_min(int* data, int n, int* warp_tmp, int hig
     const int warp = tid >> 5, lane = tid & 31, nwarps = (nt + 31) >> 5;
     int inc = warp_suffix_min(local);                 // min over this and later lanes
     if (lane == 0) warp_tmp[warp] = inc;
-    __syncthreads();
+    g.sync();
     if (warp == 0) {
         int w = lane < nwarps ? warp_tmp[lane] : highest;
         int wi = warp_suffix_min(w);
         int ex = __shfl_down_sync(0xffffffffu, wi, 1);
         if (lane < nwarps) warp_tmp[lane] = (lane + 1 < nwarps) ? ex : highest;   // min over later warps
     }
-    __syncthreads();
+    g.sync();
     int ex_thread = __shfl_down_sync(0xffffffffu, inc, 1);
     int run = min(warp_tmp[warp], lane < 31 ? ex_thread : highest);
     for (int k = hi - 1; k >= lo; --k) {
         run = min(run, data[k]);
         data[k] = run;
     }
-    __syncthreads();
+    g.sync();
 }
 
 }  // namespace lya

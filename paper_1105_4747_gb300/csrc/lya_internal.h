@@ -2,10 +2,31 @@
 // kernel launchers.  Not part of the public ABI.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
 #include "lya.h"
+
+namespace lya {
+struct FieldCheck;
+}
+
+// A field: its description and device arrays (owned or borrowed).
+struct lya_field_s {
+    lya_field_desc desc;
+    float* rho = nullptr;
+    float* vpec = nullptr;
+    float* temp = nullptr;
+    bool owned = false;
+    int* d_err = nullptr;            // device error word of extract launches
+    lya::FieldCheck* d_check = nullptr;
+    float temp_max = 0.f;            // largest T where rho > 0 (stored-T fields)
+    float rho_max = 0.f;             // largest rho
+    float rho_minpos = 0.f;          // smallest rho > 0
+    int device = 0;
+    std::atomic<int> users{0};       // server requests not yet finished
+};
 
 namespace lya {
 
@@ -34,6 +55,10 @@ struct TauLaunch {
     // FP64 forms (the FP64 comparator kernel)
     double du_d, inv_du_d, c_coef_d, h_coef_d, K_d, T0_d, gm1_d, pivot_d;
 };
+
+// Validate extraction parameters against a field and fill the field- and
+// parameter-dependent members of *out (everything but ids, n_rows, tau_out).
+lya_status make_tau_launch(lya_field f, const lya_extract_params* p, TauLaunch* out);
 
 // Launch the optical-depth kernel for the requested precision.
 cudaError_t launch_tau(const TauLaunch& L, int precision, cudaStream_t stream);

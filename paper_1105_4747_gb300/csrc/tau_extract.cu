@@ -25,6 +25,7 @@
 
 #include "lya_device.cuh"
 #include "lya_internal.h"
+#include "serve_internal.h"
 
 namespace lya {
 namespace {
@@ -279,6 +280,22 @@ constexpr int kReachHigh = 1 << 28;
 
 __host__ __device__ __forceinline__ int round_up4(int n) { return (n + 3) & ~3; }
 
+// FP32 tile gather: records | bin starts | reach | tile runs.
+__host__ __device__ inline size_t tile_smem_bytes(int n_pix, int w_max)
+{
+    const int nt = (n_pix + kTile - 1) / kTile;
+    return sizeof(float4) * (size_t)round_up4(n_pix) + sizeof(int) * (size_t)round_up4(n_pix + 1) +
+           sizeof(int) * (size_t)(n_pix + 2 * w_max) + 3 * sizeof(short) * (size_t)nt;
+}
+
+// One warp group of the serving kernel: its tile arrays, then 36 ints of scan
+// scratch and the tile-order histogram.
+constexpr int kGroupScanInts = 36;
+__host__ __device__ inline size_t group_smem_bytes(int n_pix, int w_max)
+{
+    return (tile_smem_bytes(n_pix, w_max) + 15) / 16 * 16 + sizeof(int) * (kGroupScanInts + kTileKeys);
+}
+
 // Index of the source held in register slot q: vector loads give a thread
 // four consecutive sources per group, scalar loads one source per stride.
 __device__ __forceinline__ int src_index(int q, bool vec, int tid, int nt)
@@ -337,19 +354,23 @@ __device__ __forceinline__ void pair2_segment(const float4* __restrict__ rec, in
     }
 }
 
+// One skewer by one group of threads (the whole block, or a run of warps of
+// it): rho/vpec/temp are the skewer's input rows, out its tau row.  smem
+// holds the group's tile_smem_bytes(N, w_max) bytes (16-byte aligned);
+// warp_tot (33 ints) and tile_hist (kTileKeys ints) are the group's own
+// shared scratch.  N <= MAXQ * g.nt.
 template <bool COMP, int MAXQ>
-__global__ void __launch_bounds__(512, MAXQ <= 8 ? 2 : 1) tau_tile_kernel(const TauLaunch L)
+__device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __restrict__ rho,
+                                            const float* __restrict__ vpec, const float* __restrict__ temp,
+                                            float* out, unsigned char* smem, int* warp_tot, int* tile_hist,
+                                            const Group& g)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int warp_tot[33];
-    __shared__ int tile_hist[kTileKeys];
-
     const int N = L.n_pix;
     const int Wd = L.w_max;
     const int NE = N + 2 * Wd;
     const int NT = (N + kTile - 1) / kTile;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    float4* rec = reinterpret_cast<float4*>(smem_raw);
+    const int tid = g.tid, nt = g.nt;
+    float4* rec = reinterpret_cast<float4*>(smem);
     int* bin = reinterpret_cast<int*>(rec + round_up4(N));   // N + 1 (padded to 4)
     int* reach = bin + round_up4(N + 1);                     // NE; tau once the runs are known
     float* tau_s = reinterpret_cast<float*>(reach);
@@ -357,36 +378,24 @@ __global__ void __launch_bounds__(512, MAXQ <= 8 ? 2 : 1) tau_tile_kernel(const 
     short* Rt = Lt + NT;                                     // NT
     short* order = Rt + NT;                                  // NT: tiles by candidate count
 
-    const int64_t row = blockIdx.x;
-    const int64_t sk = L.ids ? L.ids[row] : row;
-    float* out = L.tau_out + row * (int64_t)N;
-    if (sk < 0 || sk >= L.n_skewers) {
-        for (int i = tid; i < N; i += nt) out[i] = 0.f;
-        if (tid == 0) atomicOr(L.err, 1);
-        return;
-    }
-    const float* __restrict__ rho = L.rho + sk * (int64_t)N;
-    const float* __restrict__ vpec = L.vpec + sk * (int64_t)N;
-    const float* __restrict__ temp = L.temp ? L.temp + sk * (int64_t)N : nullptr;
-
     // 1. every input load issued up front (float4 when rows are 16-byte aligned)
     const bool vec = (N & 3) == 0;
     float r_[MAXQ], v_[MAXQ], T_[MAXQ];
     if (vec) {
 #pragma unroll
-        for (int g = 0; g < MAXQ / 4; ++g) {
-            const int grp = tid + g * nt;
+        for (int u4 = 0; u4 < MAXQ / 4; ++u4) {
+            const int grp = tid + u4 * nt;
             if (4 * grp < N) {
                 const float4 a = __ldcs(reinterpret_cast<const float4*>(rho) + grp);
                 const float4 b = __ldcs(reinterpret_cast<const float4*>(vpec) + grp);
                 const float4 c = temp ? __ldcs(reinterpret_cast<const float4*>(temp) + grp)
                                       : make_float4(0.f, 0.f, 0.f, 0.f);
-                r_[4 * g] = a.x; r_[4 * g + 1] = a.y; r_[4 * g + 2] = a.z; r_[4 * g + 3] = a.w;
-                v_[4 * g] = b.x; v_[4 * g + 1] = b.y; v_[4 * g + 2] = b.z; v_[4 * g + 3] = b.w;
-                T_[4 * g] = c.x; T_[4 * g + 1] = c.y; T_[4 * g + 2] = c.z; T_[4 * g + 3] = c.w;
+                r_[4 * u4] = a.x; r_[4 * u4 + 1] = a.y; r_[4 * u4 + 2] = a.z; r_[4 * u4 + 3] = a.w;
+                v_[4 * u4] = b.x; v_[4 * u4 + 1] = b.y; v_[4 * u4 + 2] = b.z; v_[4 * u4 + 3] = b.w;
+                T_[4 * u4] = c.x; T_[4 * u4 + 1] = c.y; T_[4 * u4 + 2] = c.z; T_[4 * u4 + 3] = c.w;
             } else {
 #pragma unroll
-                for (int u = 0; u < 4; ++u) r_[4 * g + u] = 0.f;
+                for (int u = 0; u < 4; ++u) r_[4 * u4 + u] = 0.f;
             }
         }
     } else {
@@ -401,7 +410,7 @@ __global__ void __launch_bounds__(512, MAXQ <= 8 ? 2 : 1) tau_tile_kernel(const 
     for (int k = tid; k <= N; k += nt) bin[k] = 0;
     for (int e = tid; e < NE; e += nt) reach[e] = kReachLow;
     for (int k = tid; k < kTileKeys; k += nt) tile_hist[k] = 0;
-    __syncthreads();
+    g.sync();
 
     // 2. per-source constants (kept in registers) and the histogram of target
     //    pixels; th_ packs (target << 16) | reach, -1 = no source
@@ -420,11 +429,11 @@ __global__ void __launch_bounds__(512, MAXQ <= 8 ? 2 : 1) tau_tile_kernel(const 
             atomicAdd(&bin[s.t + 1], 1);
         }
     }
-    __syncthreads();
+    g.sync();
 
     // 3. bin starts; scatter the records {a, c r, w, t} and every source's
     //    right reach t + h (three periodic images)
-    block_exclusive_scan(bin + 1, N, warp_tot);
+    block_exclusive_scan(bin + 1, N, warp_tot, g);
 #pragma unroll
     for (int q = 0; q < MAXQ; ++q) {
         if (th_[q] < 0) continue;
@@ -436,12 +445,12 @@ __global__ void __launch_bounds__(512, MAXQ <= 8 ? 2 : 1) tau_tile_kernel(const 
         if (t >= N - Wd) atomicMax(&reach[t - N + Wd], t - N + h);
         if (t < Wd) atomicMax(&reach[t + N + Wd], t + N + h);
     }
-    __syncthreads();
+    g.sync();
 
     // 4. first candidate bin of every tile, from the prefix max of the right reach
-    block_prefix_max(reach, NE, warp_tot, kReachLow);          // ends with a barrier
+    block_prefix_max(reach, NE, warp_tot, kReachLow, g);          // ends with a barrier
     for (int tile = tid; tile < NT; tile += nt) Lt[tile] = (short)(kTile * tile + 1);   // no source reaches it
-    __syncthreads();
+    g.sync();
     for (int e = tid; e < NE; e += nt) {
         const int prev = e ? reach[e - 1] : kReachLow;
         const int hi = min(reach[e], N - 1);
@@ -449,9 +458,9 @@ __global__ void __launch_bounds__(512, MAXQ <= 8 ? 2 : 1) tau_tile_kernel(const 
         for (int tile = max((max(prev, -4) + 1 + kTile - 1) / kTile, 0); tile * kTile <= hi; ++tile)
             Lt[tile] = (short)(e - Wd);
     }
-    __syncthreads();
+    g.sync();
     for (int e = tid; e < NE; e += nt) reach[e] = kReachHigh;
-    __syncthreads();
+    g.sync();
 #pragma unroll
     for (int q = 0; q < MAXQ; ++q) {
         if (th_[q] < 0) continue;
@@ -460,12 +469,12 @@ __global__ void __launch_bounds__(512, MAXQ <= 8 ? 2 : 1) tau_tile_kernel(const 
         if (t >= N - Wd) atomicMin(&reach[t - N + Wd], t - N - h);
         if (t < Wd) atomicMin(&reach[t + N + Wd], t + N - h);
     }
-    __syncthreads();
+    g.sync();
 
     // 5. last candidate bin of every tile, from the suffix min of the left reach
-    block_suffix_min(reach, NE, warp_tot, kReachHigh);         // ends with a barrier
+    block_suffix_min(reach, NE, warp_tot, kReachHigh, g);         // ends with a barrier
     for (int tile = tid; tile < NT; tile += nt) Rt[tile] = (short)(min(kTile * tile + kTile - 1, N - 1) - 1);
-    __syncthreads();
+    g.sync();
     for (int e = tid; e < NE; e += nt) {
         const int next = e + 1 < NE ? reach[e + 1] : kReachHigh;
         const int lo = max(reach[e], 0), hi = min(next - 1, N - 1);
@@ -473,10 +482,10 @@ __global__ void __launch_bounds__(512, MAXQ <= 8 ? 2 : 1) tau_tile_kernel(const 
         const int last = hi == N - 1 ? NT - 1 : (hi - (kTile - 1)) / kTile - (hi < kTile - 1);
         for (int tile = lo / kTile; tile <= last; ++tile) Rt[tile] = (short)(e - Wd);
     }
-    __syncthreads();
+    g.sync();
 
     // 6. tiles ordered by candidate count, largest first (counting sort)
-    constexpr int kMaxTilesPerThread = (8192 / kTile + 255) / 256;
+    constexpr int kMaxTilesPerThread = (MAXQ + kTile - 1) / kTile;   // NT <= MAXQ nt / kTile
     int tkey[kMaxTilesPerThread];
 #pragma unroll
     for (int u = 0; u < kMaxTilesPerThread; ++u) {
@@ -489,12 +498,12 @@ __global__ void __launch_bounds__(512, MAXQ <= 8 ? 2 : 1) tau_tile_kernel(const 
             atomicAdd(&tile_hist[tkey[u]], 1);
         }
     }
-    __syncthreads();
-    block_exclusive_scan(tile_hist, kTileKeys, warp_tot);
+    g.sync();
+    block_exclusive_scan(tile_hist, kTileKeys, warp_tot, g);
 #pragma unroll
     for (int u = 0; u < kMaxTilesPerThread; ++u)
         if (tkey[u] >= 0) order[atomicAdd(&tile_hist[tkey[u]], 1)] = (short)(tid + u * nt);
-    __syncthreads();
+    g.sync();
 
     // 7. lane pairs walk the tiles in that order (snaking across rounds); each
     //    lane owns two adjacent pixels; tau goes to shared memory (the reach
@@ -516,14 +525,100 @@ __global__ void __launch_bounds__(512, MAXQ <= 8 ? 2 : 1) tau_tile_kernel(const 
         if (o < N) tau_s[o] = K * (COMP ? __fsub_rn(S[0], C[0]) : S[0]);
         if (o + 1 < N) tau_s[o + 1] = K * (COMP ? __fsub_rn(S[1], C[1]) : S[1]);
     }
-    __syncthreads();
+    g.sync();
 
     // 8. tau to HBM in order
     if (vec && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
-        for (int g = tid; 4 * g < N; g += nt)
-            reinterpret_cast<float4*>(out)[g] = reinterpret_cast<const float4*>(tau_s)[g];
+        for (int k = tid; 4 * k < N; k += nt)
+            reinterpret_cast<float4*>(out)[k] = reinterpret_cast<const float4*>(tau_s)[k];
     } else {
         for (int i = tid; i < N; i += nt) out[i] = tau_s[i];
+    }
+}
+
+template <bool COMP, int MAXQ>
+__global__ void __launch_bounds__(512, MAXQ <= 8 ? 2 : 1) tau_tile_kernel(const TauLaunch L)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int warp_tot[33];
+    __shared__ int tile_hist[kTileKeys];
+    const int64_t row = blockIdx.x;
+    const int64_t sk = L.ids ? L.ids[row] : row;
+    const int N = L.n_pix;
+    float* out = L.tau_out + row * (int64_t)N;
+    if (sk < 0 || sk >= L.n_skewers) {
+        for (int i = threadIdx.x; i < N; i += blockDim.x) out[i] = 0.f;
+        if (threadIdx.x == 0) atomicOr(L.err, 1);
+        return;
+    }
+    tile_skewer<COMP, MAXQ>(L, L.rho + sk * (int64_t)N, L.vpec + sk * (int64_t)N,
+                            L.temp ? L.temp + sk * (int64_t)N : nullptr, out, smem_raw, warp_tot, tile_hist,
+                            whole_block());
+}
+
+
+// ---- serving: one persistent kernel over a step's work list ---------------------
+//
+// One 1024-thread CTA per SM takes tasks from the step's list in order (an
+// atomic counter; the list is sorted longest first).  A task is up to
+// 1 << shift skewers of one request; the CTA splits into that many warp
+// groups of 1024 >> shift threads, each with its own named barrier and its
+// own slice of shared memory, and each group extracts one skewer with the
+// same tile gather as tau_tile_kernel (compensated sums).  The request's
+// constants are copied to shared memory once per task.
+__global__ void __launch_bounds__(serve::kTauThreads, 1) tau_serve_kernel(unsigned char* __restrict__ step)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // the task and its request's constants live in shared memory, so that
+    // little but the step pointer stays in registers across the skewer body
+    __shared__ TauLaunch Ls;
+    __shared__ serve::TauTask Ts;
+    __shared__ long long s_src[1 << serve::kMaxShift], s_out[1 << serve::kMaxShift];
+    __shared__ int s_more;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            serve::StepHeader* hdr = reinterpret_cast<serve::StepHeader*>(step);
+            const int t = (int)atomicAdd(&hdr->task_next, 1u);
+            s_more = t < hdr->n_tasks;
+            if (s_more) {
+                Ts = serve::step_table<serve::TauTask>(step, hdr->off_tasks)[t];
+                const serve::TauItem* items = serve::step_table<serve::TauItem>(step, hdr->off_items);
+                for (int k = 0; k < Ts.n_items; ++k) {
+                    s_src[k] = items[Ts.first_item + k].src_row;
+                    s_out[k] = items[Ts.first_item + k].out_row;
+                }
+            }
+        }
+        __syncthreads();
+        if (!s_more) break;
+        {
+            const serve::StepHeader* hdr = reinterpret_cast<const serve::StepHeader*>(step);
+            const int* src = reinterpret_cast<const int*>(serve::step_table<TauLaunch>(step, hdr->off_slots) + Ts.slot);
+            int* dst = reinterpret_cast<int*>(&Ls);
+            for (int k = threadIdx.x; k < (int)(sizeof(TauLaunch) / sizeof(int)); k += blockDim.x) dst[k] = src[k];
+        }
+        __syncthreads();
+        const int gnt = serve::kTauThreads >> Ts.shift;
+        const int gi = (int)threadIdx.x / gnt;
+        if (gi < Ts.n_items) {
+            const Group g{(int)threadIdx.x - gi * gnt, gnt, Ts.shift == 0 ? 0 : 1 + gi};
+            const int N = Ls.n_pix;
+            unsigned char* base = smem_raw + (size_t)gi * group_smem_bytes(N, Ls.w_max);
+            int* warp_tot = reinterpret_cast<int*>(base + (tile_smem_bytes(N, Ls.w_max) + 15) / 16 * 16);
+            int* tile_hist = warp_tot + kGroupScanInts;
+            const long long src = s_src[gi];
+            float* out = Ls.tau_out + s_out[gi] * (int64_t)N;
+            if (src < 0 || src >= Ls.n_skewers) {
+                for (int i = g.tid; i < N; i += g.nt) out[i] = 0.f;
+                if (g.tid == 0) atomicOr(Ls.err, 1);
+            } else {
+                const float* rho = Ls.rho + src * (int64_t)N;
+                const float* vpec = Ls.vpec + src * (int64_t)N;
+                const float* temp = Ls.temp ? Ls.temp + src * (int64_t)N : nullptr;
+                tile_skewer<true, serve::kTauMaxQ>(Ls, rho, vpec, temp, out, base, warp_tot, tile_hist, g);
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -542,13 +637,6 @@ static size_t global_smem_bytes(int n_pix)
     return sizeof(double4_32a) * (size_t)n_pix + sizeof(int) * (size_t)(n_pix + 1);
 }
 
-// FP32 tile gather: records | bin starts | reach | tile runs.
-static size_t tile_smem_bytes(int n_pix, int w_max)
-{
-    const int nt = (n_pix + kTile - 1) / kTile;
-    return sizeof(float4) * (size_t)round_up4(n_pix) + sizeof(int) * (size_t)round_up4(n_pix + 1) +
-           sizeof(int) * (size_t)(n_pix + 2 * w_max) + 3 * sizeof(short) * (size_t)nt;
-}
 
 size_t tau_smem_bytes(int n_pix, int w_max, int precision)
 {
@@ -590,5 +678,30 @@ cudaError_t launch_tau(const TauLaunch& L, int precision, cudaStream_t stream)
     default: return cudaErrorInvalidValue;
     }
 }
+
+
+namespace serve {
+
+size_t serve_group_smem(int n_pix, int w_max) { return group_smem_bytes(n_pix, w_max); }
+
+cudaError_t serve_tau_prepare(size_t* dyn_smem)
+{
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, tau_serve_kernel);
+    if (e != cudaSuccess) return e;
+    const size_t dyn = max_dynamic_smem() - fa.sharedSizeBytes;
+    e = cudaFuncSetAttribute(tau_serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(tau_serve_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e == cudaSuccess) *dyn_smem = dyn;
+    return e;
+}
+
+cudaError_t serve_tau_launch(const unsigned char* d_step, size_t dyn_smem, int grid, cudaStream_t stream)
+{
+    tau_serve_kernel<<<grid, kTauThreads, dyn_smem, stream>>>(const_cast<unsigned char*>(d_step));
+    return cudaGetLastError();
+}
+
+}  // namespace serve
 
 }  // namespace lya
