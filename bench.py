@@ -276,12 +276,12 @@ def serve_stream(lya, srv, fields, reqs, t_end):
     return done, lag, int(t0 * 1e9)
 
 
-def run_serving(lya, torch, warm_s, measure_s, burst=400):
+def run_serving(lya, torch, warm_s, measure_s, burst=400, budget=SERVE_BUDGET):
     """p50/p99 latency and served pixels/s of the Poisson stream, and the
     loop's capacity (a burst of requests submitted at once)."""
     specs, fields = serving_pool(lya, torch)
     reqs = ls.serve_requests(len(fields), int((warm_s + measure_s) * ls.SERVE_RATE * 1.5) + burst)
-    srv = lya.Server(budget_bytes=SERVE_BUDGET, max_slots=256, step_target_us=2000.0)
+    srv = lya.Server(budget_bytes=budget, max_slots=256, step_target_us=2000.0)
     shifts = {}
     for n in ls.SERVE_N_PIX:
         k = [i for i, sp in enumerate(specs) if sp.n_pix == n]
@@ -329,7 +329,7 @@ def run_serving(lya, torch, warm_s, measure_s, burst=400):
             "submit_lag_p99_ms": float(np.percentile(np.array(lag), 99) * 1e3),
             "steps": info1["steps"] - info0["steps"], "gpu_launches": launches,
             "group_shift_by_n_pix": {str(k): v for k, v in shifts.items()},
-            "budget_bytes": SERVE_BUDGET, "latency": "submit to result (native steady clock)",
+            "budget_bytes": budget, "latency": "submit to result (native steady clock)",
             "data": "synthetic pool: boxes log-uniform 50-1000 h^-1 Mpc, n_pix 512-8192, T from each request's "
                     "power law"}
 
@@ -368,8 +368,7 @@ def run_ours(args):
         lya.extract_skewers(field, params, out=tau)
         if ev is not None:
             ev[1].record(stream)
-        A, _ = lya.rescale_mean_flux(tau, target, flux_out=F)
-        st = lya.flux_stats(F)
+        A, _, st = lya.rescale_mean_flux_stats(tau, target, flux_out=F)
         return A, st
 
     for _ in range(args.warmup):
@@ -408,8 +407,7 @@ def run_ours(args):
         def e2e_step():
             field.load(rho_h, v_h, t_h)
             lya.extract_skewers(field, params, out=tau)
-            lya.rescale_mean_flux(tau, target, flux_out=F)
-            lya.flux_stats(F)
+            lya.rescale_mean_flux_stats(tau, target, flux_out=F)
             F_h.copy_(F, non_blocking=True)
 
         e2e_step()
@@ -449,7 +447,8 @@ def run_ours(args):
     if not grid and not args.no_serving:
         del tau, F
         torch.cuda.empty_cache()
-        serving = run_serving(lya, torch, 2.0, args.serve_seconds)
+        serving = run_serving(lya, torch, 2.0, args.serve_seconds, burst=args.serve_burst,
+                              budget=int(args.serve_budget_gb * (1 << 30)))
 
     if rank == 0:
         line = {"metric": METRIC, "value": world * n_px / (ms / 1e3), "unit": UNIT, "n_gpus": world,
@@ -477,7 +476,7 @@ def run_serving_workload(args):
     import paper_1105_4747_gb300 as lya
     clocks = ClockSampler(local)
     clocks.start()
-    sv = run_serving(lya, torch, 5.0, 60.0)
+    sv = run_serving(lya, torch, 5.0, 60.0, burst=args.serve_burst, budget=int(args.serve_budget_gb * (1 << 30)))
     clk = clocks.stop()
     if rank == 0:
         line = {"metric": "served tau-skewer pixels/s, Poisson 200 req/s; p50/p99 latency", "value":
@@ -507,6 +506,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="measured seconds of the Poisson request stream in the default run")
+    ap.add_argument("--serve-burst", type=int, default=400, help="requests of the capacity burst")
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0, help="serving memory budget (GiB)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -189,6 +189,19 @@ lya_status lya_rescale_mean_flux_noalloc(const float* tau, int64_t n, double tar
                                          float* flux_out, void* stream);
 
 /*
+ * lya_rescale_mean_flux followed by lya_flux_stats of the F it writes, with
+ * the statistics gathered in the root-find's final flux pass instead of a
+ * separate read of F (Sec. 2.3, Sec. 5.2).  flux_out may be NULL (the
+ * statistics are still those of exp(-A tau) in FP32).  Arguments, results and
+ * errors are those of the two calls; stats_out must not be NULL.
+ * Synchronises the stream.
+ */
+lya_status lya_rescale_mean_flux_stats(const float* tau, int64_t n, double target_mean_flux,
+                                       double tol, int max_iter, double* A_out,
+                                       float* flux_out, lya_flux_stats_t* stats_out,
+                                       void* stream);
+
+/*
  * Per-device shares of the mean-flux root-find (Sec. 2.3) when one request's
  * pixels are split over several devices or processes: each computes its
  * share, the caller sums the shares over all parts (an all-reduce of three

@@ -28,5 +28,6 @@ from ._binding import (  # noqa: F401
     load_library,
     rescale_mean_flux,
     rescale_mean_flux_noalloc,
+    rescale_mean_flux_stats,
 )
 from .distributed import rescale_mean_flux_distributed  # noqa: F401,E402

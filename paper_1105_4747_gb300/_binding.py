@@ -107,6 +107,8 @@ def load_library():
         lib.lya_extract_skewers.argtypes = [vp, ctypes.POINTER(_ExtractParams), vp, i64, vp, vp]
         lib.lya_rescale_mean_flux.argtypes = [vp, i64, d, d, i32, ctypes.POINTER(d), vp, vp]
         lib.lya_rescale_mean_flux_noalloc.argtypes = [vp, i64, d, d, i32, ctypes.POINTER(d), vp, vp]
+        lib.lya_rescale_mean_flux_stats.argtypes = [vp, i64, d, d, i32, ctypes.POINTER(d), vp,
+                                                    ctypes.POINTER(_FluxStats), vp]
         lib.lya_flux_stats.argtypes = [vp, i64, ctypes.POINTER(_FluxStats), vp]
         lib.lya_tau_moments.argtypes = [vp, i64, ctypes.POINTER(d), vp]
         lib.lya_mean_flux_sums.argtypes = [vp, i64, d, ctypes.POINTER(d), vp]
@@ -123,7 +125,7 @@ def load_library():
         lib.lya_server_destroy.argtypes = [vp]
         for name in ("lya_create_field", "lya_field_load", "lya_destroy_field", "lya_field_status",
                      "lya_field_shape", "lya_extract_skewers", "lya_rescale_mean_flux",
-                     "lya_rescale_mean_flux_noalloc", "lya_flux_stats", "lya_tau_moments",
+                     "lya_rescale_mean_flux_noalloc", "lya_rescale_mean_flux_stats", "lya_flux_stats", "lya_tau_moments",
                      "lya_mean_flux_sums", "lya_flux_at", "lya_server_create", "lya_server_autotune",
                      "lya_server_submit", "lya_server_poll", "lya_server_wait", "lya_server_copy_flux",
                      "lya_server_release", "lya_server_info", "lya_server_destroy"):
@@ -302,6 +304,27 @@ def rescale_mean_flux(tau, target: float, tol: float = 1e-12, max_iter: int = 50
                                                 F.data_ptr() if F is not None else None,
                                                 _stream_handle(stream)), "lya_rescale_mean_flux")
     return A.value, F
+
+
+def rescale_mean_flux_stats(tau, target: float, tol: float = 1e-12, max_iter: int = 50, flux_out=True,
+                            stream=None):
+    """lya_rescale_mean_flux_stats: (A, F or None, FluxStats) with the statistics
+    gathered in the root-find's final flux pass."""
+    torch = _torch()
+    _require_cuda_f32(tau, "tau")
+    F = None
+    if flux_out is True:
+        F = torch.empty_like(tau)
+    elif flux_out is not None and flux_out is not False:
+        F = _require_cuda_f32(flux_out, "flux_out")
+    A = ctypes.c_double(math.nan)
+    out = _FluxStats()
+    _check(load_library().lya_rescale_mean_flux_stats(tau.data_ptr(), tau.numel(), float(target), float(tol),
+                                                      int(max_iter), ctypes.byref(A),
+                                                      F.data_ptr() if F is not None else None, ctypes.byref(out),
+                                                      _stream_handle(stream)), "lya_rescale_mean_flux_stats")
+    st = FluxStats(out.mean_flux, out.var_flux, out.tau_eff, np.array(out.pdf[:], dtype=np.int64), out.n)
+    return A.value, F, st
 
 
 def rescale_mean_flux_noalloc(tau, target: float, flux_out, tol: float = 1e-12, max_iter: int = 50,

@@ -329,6 +329,16 @@ lya_status lya_rescale_mean_flux(const float* tau, int64_t n, double target, dou
                                 static_cast<cudaStream_t>(stream));
 }
 
+lya_status lya_rescale_mean_flux_stats(const float* tau, int64_t n, double target, double tol, int max_iter,
+                                       double* A_out, float* flux_out, lya_flux_stats_t* stats_out, void* stream)
+{
+    if (!tau || n <= 0 || !A_out || !stats_out) return LYA_EINVAL;
+    if (!(target > 0.0 && target < 1.0)) return LYA_EINVAL;
+    if (!(tol > 0.0) || max_iter < 1) return LYA_EINVAL;
+    return lya::mean_flux_solve(tau, n, target, tol, max_iter, A_out, flux_out,
+                                static_cast<cudaStream_t>(stream), stats_out);
+}
+
 lya_status lya_rescale_mean_flux_noalloc(const float* tau, int64_t n, double target, double tol,
                                          int max_iter, double* A_out, float* flux_out, void* stream)
 {

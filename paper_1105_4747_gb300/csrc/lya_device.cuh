@@ -83,6 +83,11 @@ struct Group {
 
 __device__ __forceinline__ Group whole_block() { return Group{(int)threadIdx.x, (int)blockDim.x, 0}; }
 
+// Each thread of a scan owns a contiguous chunk of the array.  The chunk
+// length is odd, so the 32 lanes of a warp, one chunk apart, fall in 32
+// different shared-memory banks.
+__device__ __forceinline__ int scan_chunk(int n, int nt) { return ((n + nt - 1) / nt) | 1; }
+
 // In-place exclusive scan of data[0..n) (ints in shared memory) by the
 // group; returns the total on every thread.  warp_tot holds >= 33 ints of
 // shared scratch private to the group.  Synchronises the group: call from
@@ -91,7 +96,7 @@ __device__ inline int block_exclusive_scan(int* data, int n, int* warp_tot, cons
 {
     const int nt = g.nt;
     const int tid = g.tid;
-    const int per = (n + nt - 1) / nt;
+    const int per = scan_chunk(n, nt);
     const int lo = min(n, tid * per), hi = min(n, lo + per);
     int local = 0;
     for (int k = lo; k < hi; ++k) local += data[k];
@@ -150,7 +155,7 @@ __device__ __forceinline__ int warp_suffix_min(int v)
 __device__ inline void block_prefix_max(int* data, int n, int* warp_tmp, int lowest, const Group& g)
 {
     const int nt = g.nt, tid = g.tid;
-    const int per = (n + nt - 1) / nt;
+    const int per = scan_chunk(n, nt);
     const int lo = min(n, tid * per), hi = min(n, lo + per);
     int local = lowest;
     for (int k = lo; k < hi; ++k) local = max(local, data[k]);
@@ -179,7 +184,7 @@ __device__ inline void block_prefix_max(int* data, int n, int* warp_tmp, int low
 __device__ inline void block_suffix_min(int* data, int n, int* warp_tmp, int highest, const Group& g)
 {
     const int nt = g.nt, tid = g.tid;
-    const int per = (n + nt - 1) / nt;
+    const int per = scan_chunk(n, nt);
     const int lo = min(n, tid * per), hi = min(n, lo + per);
     int local = highest;
     for (int k = lo; k < hi; ++k) local = min(local, data[k]);

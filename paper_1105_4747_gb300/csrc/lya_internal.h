@@ -72,9 +72,11 @@ size_t max_dynamic_smem();
 
 // Mean-flux root-find (Sec. 2.3) over n device values of tau; writes A to
 // *A_out and, if flux_out is not null, F = exp(-A tau).  Returns a lya_status.
+// With stats_out, the final flux pass also gathers the statistics of F
+// (Sec. 2.3, 5.2) into *stats_out.
 lya_status mean_flux_solve(const float* tau, int64_t n, double target, double tol,
                            int max_iter, double* A_out, float* flux_out,
-                           cudaStream_t stream);
+                           cudaStream_t stream, lya_flux_stats_t* stats_out = nullptr);
 
 // The same root-find with its scratch in a fixed device array (no allocation).
 lya_status mean_flux_solve_noalloc(const float* tau, int64_t n, double target, double tol,

@@ -102,40 +102,99 @@ __global__ void __launch_bounds__(kThreads) mf_newton_kernel(const float* __rest
     if (threadIdx.x == 0) halley_update(st, tot[0], tot[1], tot[2], tot[3]);
 }
 
-// ---- F = exp(-A tau), and the convergence check at that A ------------------------
+// ---- F = exp(-A tau), the convergence check at that A and, optionally, the
+//      statistics of that F (kept only when the check passes) ---------------
+struct StatsOut {
+    double m1, m2;                // sums of (F - 0.5) and (F - 0.5)^2
+    unsigned long long pdf[21];
+    unsigned int ticket;
+};
+
+template <bool STATS>
 __global__ void __launch_bounds__(kThreads) mf_flux_kernel(const float* __restrict__ tau, long long n,
-                                                         MFState* st, Partial* part, float* __restrict__ F)
+                                                         MFState* st, Partial* part, float* __restrict__ F,
+                                                         StatPart* spart, StatsOut* sout)
 {
     if (st->done && st->status != LYA_OK) return;    // an error is final
+    // one private 21-bin counter row per thread (21 is odd: conflict-free)
+    __shared__ unsigned int cnt[STATS ? kThreads * 21 : 1];
+    unsigned int* mine = cnt + (STATS ? threadIdx.x * 21 : 0);
+    if constexpr (STATS)
+        for (int k = 0; k < 21; ++k) mine[k] = 0;
     float a_hi, a_lo;
     split_rate(st->A, a_hi, a_lo);
-    KahanF32 s0;
+    KahanF32 s0, m1, m2;
     float s0c = 0.f;
     stream_f32(tau, n, [&](long long i, float t) {
         float e, c;
         exp_neg(t, a_hi, a_lo, e, c);
-        if (F) F[i] = e + c;
+        const float f = e + c;
+        if (F) F[i] = f;
         s0.add(e);
         s0c += c;
+        if constexpr (STATS) {
+            const float d = f - 0.5f;
+            m1.add(d);
+            m2.add(d * d);
+            mine[pdf_bin(f)] += 1u;
+        }
     });
-    __shared__ double sh[2][32];
-    double v[2] = {(double)s0.value(), (double)s0c};
-    block_sum<2>(v, sh);
+    constexpr int K = STATS ? 4 : 2;
+    __shared__ double sh[K][32];
+    double v[K];
+    v[0] = (double)s0.value();
+    v[1] = (double)s0c;
+    if constexpr (STATS) {
+        v[2] = (double)m1.value();
+        v[3] = (double)m2.value();
+    }
+    block_sum<K>(v, sh);                                     // ends with a barrier
+    if constexpr (STATS) {
+        for (int k = threadIdx.x; k < 21; k += blockDim.x) {
+            unsigned int c = 0;
+            for (int r = 0; r < (int)blockDim.x; ++r) c += cnt[r * 21 + k];
+            spart[blockIdx.x].pdf[k] = c;
+        }
+        if (threadIdx.x == 0) {
+            spart[blockIdx.x].m1 = v[2];
+            spart[blockIdx.x].m2 = v[3];
+        }
+    }
     if (threadIdx.x == 0) part[blockIdx.x] = Partial{v[0], v[1], 0.0, 0.0, 0, 0};
     if (!last_block(&st->ticket)) return;
     double tot[2];
     partial_totals<2>(part, gridDim.x, tot, sh, [](const Partial& p, double (&x)[2]) {
         x[0] = p.s0; x[1] = p.s0c;
     });
-    if (threadIdx.x == 0) flux_update(st, tot[0], tot[1]);
+    if constexpr (!STATS) {
+        if (threadIdx.x == 0) flux_update(st, tot[0], tot[1]);
+    } else {
+        __shared__ int s_final;
+        if (threadIdx.x == 0) {
+            flux_update(st, tot[0], tot[1]);
+            s_final = st->done && st->status == LYA_OK;
+        }
+        __syncthreads();
+        if (!s_final) return;
+        double ms[2] = {0.0, 0.0};
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+            ms[0] += spart[b].m1;
+            ms[1] += spart[b].m2;
+        }
+        block_sum<2>(ms, sh);
+        for (int k = threadIdx.x; k < 21; k += blockDim.x) {
+            unsigned long long c = 0;
+            for (int b = 0; b < (int)gridDim.x; ++b) c += spart[b].pdf[k];
+            sout->pdf[k] = c;
+        }
+        if (threadIdx.x == 0) {
+            sout->m1 = ms[0];
+            sout->m2 = ms[1];
+        }
+    }
 }
 
 // ---- flux statistics -----------------------------------------------------------------
-struct StatsOut {
-    double m1, m2;                // sums of (F - 0.5) and (F - 0.5)^2
-    unsigned long long pdf[21];
-    unsigned int ticket;
-};
 
 __global__ void __launch_bounds__(kThreads) stats_kernel(const float* __restrict__ F, long long n,
                                                        StatsOut* out, double* part)
@@ -290,7 +349,8 @@ namespace {
 // per round.
 static lya_status solve_on_scratch(const float* tau, int64_t n, double target, double tol, int max_iter,
                                    double* A_out, float* flux_out, MFState* st, Partial* part, int grid,
-                                   cudaStream_t stream)
+                                   cudaStream_t stream, StatPart* spart = nullptr, StatsOut* sout = nullptr,
+                                   lya_flux_stats_t* stats_out = nullptr)
 {
     static_assert(sizeof(MFState) % 8 == 0, "state layout");
     MFState hs{};                                   // host copy (no heap allocation)
@@ -315,7 +375,10 @@ static lya_status solve_on_scratch(const float* tau, int64_t n, double target, d
             err = cudaGetLastError();
         }
         if (err != cudaSuccess) break;
-        mf_flux_kernel<<<grid, kThreads, 0, stream>>>(tau, n, st, part, flux_out);
+        if (spart)
+            mf_flux_kernel<true><<<grid, kThreads, 0, stream>>>(tau, n, st, part, flux_out, spart, sout);
+        else
+            mf_flux_kernel<false><<<grid, kThreads, 0, stream>>>(tau, n, st, part, flux_out, nullptr, nullptr);
         count_launch();
         err = cudaGetLastError();
         if (err == cudaSuccess) err = cudaMemcpyAsync(h, st, offsetof(MFState, hist), cudaMemcpyDeviceToHost, stream);
@@ -331,6 +394,20 @@ static lya_status solve_on_scratch(const float* tau, int64_t n, double target, d
         }
     }
     if (err == cudaSuccess && result == LYA_OK) *A_out = h->A;
+    if (err == cudaSuccess && result == LYA_OK && stats_out) {
+        StatsOut hs2{};
+        err = cudaMemcpyAsync(&hs2, sout, sizeof(StatsOut), cudaMemcpyDeviceToHost, stream);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(stream);
+        if (err == cudaSuccess) {
+            const double nn = (double)n;
+            const double m1 = hs2.m1 / nn, m2 = hs2.m2 / nn;
+            stats_out->mean_flux = 0.5 + m1;
+            stats_out->var_flux = m2 - m1 * m1;
+            stats_out->tau_eff = -log(stats_out->mean_flux);
+            for (int k = 0; k < 21; ++k) stats_out->pdf[k] = (int64_t)hs2.pdf[k];
+            stats_out->n = n;
+        }
+    }
     if (err != cudaSuccess) return err == cudaErrorMemoryAllocation ? LYA_ENOMEM : LYA_ECUDA;
     return result;
 }
@@ -338,18 +415,25 @@ static lya_status solve_on_scratch(const float* tau, int64_t n, double target, d
 }  // namespace
 
 lya_status mean_flux_solve(const float* tau, int64_t n, double target, double tol, int max_iter,
-                           double* A_out, float* flux_out, cudaStream_t stream)
+                           double* A_out, float* flux_out, cudaStream_t stream, lya_flux_stats_t* stats_out)
 {
     const int grid = grid_for(n);
     MFState* st = nullptr;
     Partial* part = nullptr;
+    StatPart* spart = nullptr;
+    StatsOut* sout = nullptr;
     cudaError_t err = cudaMallocAsync((void**)&st, sizeof(MFState), stream);
     if (err == cudaSuccess) err = cudaMallocAsync((void**)&part, sizeof(Partial) * grid, stream);
+    if (err == cudaSuccess && stats_out) err = cudaMallocAsync((void**)&spart, sizeof(StatPart) * grid, stream);
+    if (err == cudaSuccess && stats_out) err = cudaMallocAsync((void**)&sout, sizeof(StatsOut), stream);
     lya_status result = err == cudaSuccess
-        ? solve_on_scratch(tau, n, target, tol, max_iter, A_out, flux_out, st, part, grid, stream)
+        ? solve_on_scratch(tau, n, target, tol, max_iter, A_out, flux_out, st, part, grid, stream, spart, sout,
+                           stats_out)
         : (err == cudaErrorMemoryAllocation ? LYA_ENOMEM : LYA_ECUDA);
     if (st) cudaFreeAsync(st, stream);
     if (part) cudaFreeAsync(part, stream);
+    if (spart) cudaFreeAsync(spart, stream);
+    if (sout) cudaFreeAsync(sout, stream);
     if (cudaStreamSynchronize(stream) != cudaSuccess && result == LYA_OK) result = LYA_ECUDA;
     return result;
 }

@@ -75,6 +75,14 @@ struct Partial {
     long long z, bad;
 };
 
+// One CTA's share of the flux statistics: sums of (F - 1/2), (F - 1/2)^2 and
+// the 21 PDF bin counts.
+struct StatPart {
+    double m1, m2;
+    unsigned int pdf[21];
+    unsigned int pad;
+};
+
 __device__ __forceinline__ double warp_sum_d(double v)
 {
 #pragma unroll

@@ -23,12 +23,6 @@ namespace {
 
 using namespace mfd;
 
-struct StatPartial {
-    double m1, m2;
-    unsigned int pdf[21];
-    unsigned int pad;
-};
-
 struct View {
     const StepHeader* hdr;
     const RfSlot* rf;
@@ -179,7 +173,7 @@ __global__ void __launch_bounds__(kRfThreads) rf_halley_kernel(const unsigned ch
 // statistics of the request when the check passes.
 __global__ void __launch_bounds__(kRfThreads) rf_flux_kernel(const unsigned char* __restrict__ step,
                                                            MFState* states, SlotResult* results, Partial* part,
-                                                           StatPartial* spart)
+                                                           StatPart* spart)
 {
     const View v(step);
     // one private 21-bin counter row per thread (21 is odd: conflict-free)
@@ -234,7 +228,7 @@ __global__ void __launch_bounds__(kRfThreads) rf_flux_kernel(const unsigned char
         if (!last_arrival(&st->ticket, (unsigned)s.unit_count)) continue;
         double tot[4];
         const Partial* pp = part + s.unit_first;
-        const StatPartial* sp = spart + s.unit_first;
+        const StatPart* sp = spart + s.unit_first;
         for (int k = 0; k < 4; ++k) tot[k] = 0.0;
         for (int b = threadIdx.x; b < s.unit_count; b += blockDim.x) {
             tot[0] += pp[b].s0;
@@ -269,14 +263,14 @@ __global__ void __launch_bounds__(kRfThreads) rf_flux_kernel(const unsigned char
 
 size_t serve_state_bytes() { return sizeof(MFState); }
 size_t serve_part_bytes() { return sizeof(Partial); }
-size_t serve_spart_bytes() { return sizeof(StatPartial); }
+size_t serve_spart_bytes() { return sizeof(StatPart); }
 
 cudaError_t serve_rf_launch(const unsigned char* d_step, void* d_states, SlotResult* d_results, void* d_part,
                             void* d_spart, int grid, cudaStream_t stream, int* n_launched)
 {
     MFState* st = static_cast<MFState*>(d_states);
     Partial* part = static_cast<Partial*>(d_part);
-    StatPartial* sp = static_cast<StatPartial*>(d_spart);
+    StatPart* sp = static_cast<StatPart*>(d_spart);
     int n = 0;
     rf_reset_kernel<<<64, kRfThreads, 0, stream>>>(d_step, st, d_results);
     ++n;

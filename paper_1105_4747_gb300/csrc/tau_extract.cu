@@ -2,7 +2,7 @@
 //
 // One CTA owns one skewer.  Two kernels:
 //   * tau_tile_kernel (FP32, the product path): sources counting-sorted by
-//     target pixel; lane pairs own four-pixel tiles, taken in order of
+//     target pixel; four lanes share an eight-pixel tile, taken in order of
 //     candidate count, and sum the sources whose reach covers the tile
 //     (compensated or plain);
 //   * tau_kernel (FP64 comparator): sources counting-sorted by target pixel,
@@ -255,28 +255,32 @@ __global__ void __launch_bounds__(512) tau_kernel(const TauLaunch L)
 //   L = first bin t with max_{t' <= t}(t' + h_t') >= first pixel of the tile
 //   R = last  bin t with min_{t' >= t}(t' - h_t') <= last pixel of the tile
 // (prefix max of the right reach, suffix min of the left reach, over bins
-// extended by w_max on both sides so the periodic wrap is explicit).  This
-// holds every source covering the tile and, away from the broadest lines,
-// little else.
+// extended by w_max on both sides so the periodic wrap is explicit).  Both
+// are monotone, and h <= w_max confines L and R of the tile at pixels
+// [lo, hi] to the extended bins [lo, hi + 2 w_max]: a binary search there
+// finds them.  The run holds every source covering the tile and, away from
+// the broadest lines, little else.
 //
 // Load balance: the tiles are counting-sorted by candidate count, largest
-// first, and handed to lane pairs in that order, so the sixteen pairs of a
-// warp walk lists of nearly equal length.  Each lane owns two adjacent pixels
-// of its tile: a candidate record is read once from shared memory and
-// evaluated for both (one MUFU ex2 each).  tau is gathered in shared memory
-// and written to HBM in order at the end.
+// first, and handed to the threads in that order (reversed on alternate
+// rounds), so the lanes of a warp walk lists of nearly equal length.  Four
+// lanes share a tile and each owns two adjacent pixels: a candidate record is
+// read once from shared memory and evaluated for both (one MUFU ex2 each).
+// tau is gathered in shared memory and written to HBM in order at the end.
 //
 // Accumulation per pixel: the terms of four consecutive candidates are added
 // plainly, then folded into a Kahan sum (compensated variant); or every term
 // is added plainly (naive variant).
 //
-// Shared memory: records (N rounded up to 4) | bin starts (N+1, padded to 4) |
-// reach (N + 2 w_max; later tau) | tile runs L, R and the tile order (int16).
-constexpr int kTile = 4;
-constexpr int kLanesPerTile = 2;                 // each lane: kTile / kLanesPerTile pixels
+// Shared memory: records (N rounded up to 4) | bin counts (4 + N rounded up
+// to 4; the leading zero makes bin starts and ends one array) | reach (N + 2
+// w_max; later tau) | tile runs L, R and the tile order (int16).
+constexpr int kTile = 8;
+constexpr int kLanesPerTile = 4;                 // each lane: kTile / kLanesPerTile = 2 pixels
 constexpr int kTileKeys = 256;                   // tile-order histogram (counts >= 255 share a key)
 constexpr int kReachLow = -(1 << 28);
 constexpr int kReachHigh = 1 << 28;
+constexpr int kEmptyRun = 30000;                 // L of a tile no source reaches (L > R)
 
 __host__ __device__ __forceinline__ int round_up4(int n) { return (n + 3) & ~3; }
 
@@ -284,7 +288,7 @@ __host__ __device__ __forceinline__ int round_up4(int n) { return (n + 3) & ~3; 
 __host__ __device__ inline size_t tile_smem_bytes(int n_pix, int w_max)
 {
     const int nt = (n_pix + kTile - 1) / kTile;
-    return sizeof(float4) * (size_t)round_up4(n_pix) + sizeof(int) * (size_t)round_up4(n_pix + 1) +
+    return sizeof(float4) * (size_t)round_up4(n_pix) + sizeof(int) * (size_t)(4 + round_up4(n_pix)) +
            sizeof(int) * (size_t)(n_pix + 2 * w_max) + 3 * sizeof(short) * (size_t)nt;
 }
 
@@ -316,6 +320,35 @@ __device__ __forceinline__ void for_tile_run(const int* bin, int N, int lx, int 
     if (rx >= N) f(bin[max(lx, N) - N], bin[rx - N + 1], -(float)N);
 }
 
+// Binary searches over a non-decreasing int array v on [a, b]: the first
+// index with v >= x (b + 1 if none), the last with v <= x (a - 1 if none).
+__device__ __forceinline__ int first_at_least(const int* v, int a, int b, int x)
+{
+    int lo = a, hi = b + 1;
+    while (lo < hi) {
+        const int m = (lo + hi) >> 1;
+        if (v[m] >= x) hi = m; else lo = m + 1;
+    }
+    return lo;
+}
+__device__ __forceinline__ int last_at_most(const int* v, int a, int b, int x)
+{
+    int lo = a, hi = b + 1;
+    while (lo < hi) {
+        const int m = (lo + hi) >> 1;
+        if (v[m] > x) hi = m; else lo = m + 1;
+    }
+    return lo - 1;
+}
+
+__device__ __forceinline__ void kahan_fold(float& S, float& C, float P)
+{
+    const float y = __fsub_rn(P, C);
+    const float t = __fadd_rn(S, y);
+    C = __fsub_rn(__fsub_rn(t, S), y);
+    S = t;
+}
+
 // Two adjacent pixels fo, fo + 1 (in the run's frame) against candidates [k0, k1).
 template <bool COMP>
 __device__ __forceinline__ void pair2_segment(const float4* __restrict__ rec, int k0, int k1, float fo,
@@ -323,7 +356,7 @@ __device__ __forceinline__ void pair2_segment(const float4* __restrict__ rec, in
 {
     int k = k0;
     if constexpr (COMP) {
-        for (; k < k1;) {
+        while (k < k1) {
             float P0 = 0.f, P1 = 0.f;
             const int kk = min(k + 4, k1);
             for (; k < kk; ++k) {
@@ -333,14 +366,8 @@ __device__ __forceinline__ void pair2_segment(const float4* __restrict__ rec, in
                 P0 = fmaf(r.z, ex2(-(x0 * x0)), P0);
                 P1 = fmaf(r.z, ex2(-(x1 * x1)), P1);
             }
-            float y = __fsub_rn(P0, C[0]);                   // Kahan folds of the block sums
-            float t = __fadd_rn(S[0], y);
-            C[0] = __fsub_rn(__fsub_rn(t, S[0]), y);
-            S[0] = t;
-            y = __fsub_rn(P1, C[1]);
-            t = __fadd_rn(S[1], y);
-            C[1] = __fsub_rn(__fsub_rn(t, S[1]), y);
-            S[1] = t;
+            kahan_fold(S[0], C[0], P0);                      // Kahan folds of the block sums
+            kahan_fold(S[1], C[1], P1);
         }
     } else {
 #pragma unroll 2
@@ -357,8 +384,8 @@ __device__ __forceinline__ void pair2_segment(const float4* __restrict__ rec, in
 // One skewer by one group of threads (the whole block, or a run of warps of
 // it): rho/vpec/temp are the skewer's input rows, out its tau row.  smem
 // holds the group's tile_smem_bytes(N, w_max) bytes (16-byte aligned);
-// warp_tot (33 ints) and tile_hist (kTileKeys ints) are the group's own
-// shared scratch.  N <= MAXQ * g.nt.
+// warp_tot (33 ints) and tile_hist (kTileKeys ints, 16-byte aligned) are the
+// group's own shared scratch.  N <= MAXQ * g.nt.
 template <bool COMP, int MAXQ>
 __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __restrict__ rho,
                                             const float* __restrict__ vpec, const float* __restrict__ temp,
@@ -371,8 +398,10 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
     const int NT = (N + kTile - 1) / kTile;
     const int tid = g.tid, nt = g.nt;
     float4* rec = reinterpret_cast<float4*>(smem);
-    int* bin = reinterpret_cast<int*>(rec + round_up4(N));   // N + 1 (padded to 4)
-    int* reach = bin + round_up4(N + 1);                     // NE; tau once the runs are known
+    int* cnt = reinterpret_cast<int*>(rec + round_up4(N)) + 4;   // N (padded to 4), cnt[-1] = 0
+    int* bin = cnt - 1;                                          // after the scatter: bin[t] = start(t),
+                                                                 // bin[t + 1] = end(t)
+    int* reach = cnt + round_up4(N);                         // NE; tau once the runs are known
     float* tau_s = reinterpret_cast<float*>(reach);
     short* Lt = reinterpret_cast<short*>(reach + NE);        // NT
     short* Rt = Lt + NT;                                     // NT
@@ -407,7 +436,7 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
             T_[q] = (j < N && temp) ? __ldcs(temp + j) : 0.f;
         }
     }
-    for (int k = tid; k <= N; k += nt) bin[k] = 0;
+    for (int k = tid - 4; k < N; k += nt) cnt[k] = 0;
     for (int e = tid; e < NE; e += nt) reach[e] = kReachLow;
     for (int k = tid; k < kTileKeys; k += nt) tile_hist[k] = 0;
     g.sync();
@@ -426,19 +455,19 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
             bb_[q] = s.bb;
             w_[q] = s.w;
             th_[q] = (s.t << 16) | s.h;
-            atomicAdd(&bin[s.t + 1], 1);
+            atomicAdd(&cnt[s.t], 1);
         }
     }
     g.sync();
 
     // 3. bin starts; scatter the records {a, c r, w, t} and every source's
     //    right reach t + h (three periodic images)
-    block_exclusive_scan(bin + 1, N, warp_tot, g);
+    block_exclusive_scan(cnt, N, warp_tot, g);
 #pragma unroll
     for (int q = 0; q < MAXQ; ++q) {
         if (th_[q] < 0) continue;
         const int t = th_[q] >> 16, h = th_[q] & 0xffff;
-        const int pos = atomicAdd(&bin[t + 1], 1);
+        const int pos = atomicAdd(&cnt[t], 1);
         if (pos >= N) { atomicOr(L.err, 2); th_[q] = -1; continue; }   // input changed under the kernel
         rec[pos] = make_float4(a_[q], bb_[q], w_[q], (float)t);
         atomicMax(&reach[t + Wd], t + h);
@@ -447,16 +476,12 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
     }
     g.sync();
 
-    // 4. first candidate bin of every tile, from the prefix max of the right reach
-    block_prefix_max(reach, NE, warp_tot, kReachLow, g);          // ends with a barrier
-    for (int tile = tid; tile < NT; tile += nt) Lt[tile] = (short)(kTile * tile + 1);   // no source reaches it
-    g.sync();
-    for (int e = tid; e < NE; e += nt) {
-        const int prev = e ? reach[e - 1] : kReachLow;
-        const int hi = min(reach[e], N - 1);
-        if (hi < 0) continue;
-        for (int tile = max((max(prev, -4) + 1 + kTile - 1) / kTile, 0); tile * kTile <= hi; ++tile)
-            Lt[tile] = (short)(e - Wd);
+    // 4. first candidate bin of every tile: search the prefix max of the right reach
+    block_prefix_max(reach, NE, warp_tot, kReachLow, g);       // ends with a barrier
+    for (int tile = tid; tile < NT; tile += nt) {
+        const int lo = kTile * tile, hi = min(lo + kTile - 1, N - 1);
+        const int e = first_at_least(reach, lo, min(hi + 2 * Wd, NE - 1), lo);
+        Lt[tile] = (short)(e <= min(hi + 2 * Wd, NE - 1) ? e - Wd : kEmptyRun);
     }
     g.sync();
     for (int e = tid; e < NE; e += nt) reach[e] = kReachHigh;
@@ -471,16 +496,12 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
     }
     g.sync();
 
-    // 5. last candidate bin of every tile, from the suffix min of the left reach
-    block_suffix_min(reach, NE, warp_tot, kReachHigh, g);         // ends with a barrier
-    for (int tile = tid; tile < NT; tile += nt) Rt[tile] = (short)(min(kTile * tile + kTile - 1, N - 1) - 1);
-    g.sync();
-    for (int e = tid; e < NE; e += nt) {
-        const int next = e + 1 < NE ? reach[e + 1] : kReachHigh;
-        const int lo = max(reach[e], 0), hi = min(next - 1, N - 1);
-        if (lo > hi) continue;
-        const int last = hi == N - 1 ? NT - 1 : (hi - (kTile - 1)) / kTile - (hi < kTile - 1);
-        for (int tile = lo / kTile; tile <= last; ++tile) Rt[tile] = (short)(e - Wd);
+    // 5. last candidate bin of every tile: search the suffix min of the left reach
+    block_suffix_min(reach, NE, warp_tot, kReachHigh, g);      // ends with a barrier
+    for (int tile = tid; tile < NT; tile += nt) {
+        const int lo = kTile * tile, hi = min(lo + kTile - 1, N - 1);
+        const int e = last_at_most(reach, lo, min(hi + 2 * Wd, NE - 1), hi);
+        Rt[tile] = (short)(e >= lo ? e - Wd : -kEmptyRun);
     }
     g.sync();
 
@@ -492,9 +513,9 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
         const int tile = tid + u * nt;
         tkey[u] = -1;
         if (tile < NT) {
-            int cnt = 0;
-            for_tile_run(bin, N, Lt[tile], Rt[tile], [&](int k0, int k1, float) { cnt += k1 - k0; });
-            tkey[u] = kTileKeys - 1 - min(cnt, kTileKeys - 1);
+            int c = 0;
+            for_tile_run(bin, N, Lt[tile], Rt[tile], [&](int k0, int k1, float) { c += k1 - k0; });
+            tkey[u] = kTileKeys - 1 - min(c, kTileKeys - 1);
             atomicAdd(&tile_hist[tkey[u]], 1);
         }
     }
@@ -505,15 +526,13 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
         if (tkey[u] >= 0) order[atomicAdd(&tile_hist[tkey[u]], 1)] = (short)(tid + u * nt);
     g.sync();
 
-    // 7. lane pairs walk the tiles in that order (snaking across rounds); each
-    //    lane owns two adjacent pixels; tau goes to shared memory (the reach
-    //    array is free now)
+    // 7. lane groups walk the tiles in that order (reversed on alternate
+    //    rounds, so every warp's total work evens out); each lane owns two
+    //    adjacent pixels; tau goes to shared memory (the reach array is free)
     const int lane_q = tid & (kLanesPerTile - 1);
     const float K = L.K;
     const int npairs = nt / kLanesPerTile, pair = tid / kLanesPerTile;
     for (int round = 0; round * npairs < NT; ++round) {
-        // snake order: alternate rounds run the largest tiles on the last
-        // pairs, so every warp's total work evens out across rounds
         const int i = round * npairs + ((round & 1) ? npairs - 1 - pair : pair);
         if (i >= NT) continue;
         const int tile = order[i];
@@ -541,7 +560,7 @@ __global__ void __launch_bounds__(512, MAXQ <= 8 ? 2 : 1) tau_tile_kernel(const 
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int warp_tot[33];
-    __shared__ int tile_hist[kTileKeys];
+    __shared__ __align__(16) int tile_hist[kTileKeys];
     const int64_t row = blockIdx.x;
     const int64_t sk = L.ids ? L.ids[row] : row;
     const int N = L.n_pix;

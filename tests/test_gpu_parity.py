@@ -376,3 +376,22 @@ def test_split_root_find_matches_single_device(lya, orc):
     F = torch.cat([lya.flux_at(h, A2) for h in halves])
     torch.cuda.synchronize()
     assert float((F - F_ref).abs().max()) <= 1e-6
+
+
+def test_fused_stats_equal_separate_call(lya):
+    """lya_rescale_mean_flux_stats gives the A and F of lya_rescale_mean_flux and
+    the statistics lya_flux_stats computes from that F."""
+    spec = ls.TINY_20MPC
+    rho, v, t = ls.skewers(spec, np.arange(ls.TINY_20MPC_SKEWERS))
+    field = make_field(lya, spec, rho, v, t)
+    tau = lya.extract_skewers(field, lya.ExtractParams())
+    A1, F1 = lya.rescale_mean_flux(tau, ls.TINY_20MPC_FT)
+    st1 = lya.flux_stats(F1)
+    A2, F2, st2 = lya.rescale_mean_flux_stats(tau, ls.TINY_20MPC_FT)
+    assert A2 == A1
+    assert bool((F1 == F2).all())
+    assert np.array_equal(st1.pdf, st2.pdf) and st1.n == st2.n
+    assert st2.mean_flux == pytest.approx(st1.mean_flux, rel=1e-12)
+    assert st2.var_flux == pytest.approx(st1.var_flux, rel=1e-9)
+    A3, F3, st3 = lya.rescale_mean_flux_stats(tau, ls.TINY_20MPC_FT, flux_out=None)
+    assert F3 is None and A3 == A1 and np.array_equal(st3.pdf, st1.pdf)
