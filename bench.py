@@ -42,12 +42,11 @@ WORKLOAD = "gpc_box_65536x4096_z2.5"
 ALG_BYTES_PER_PX = 16          # rho, vpec, T read (12 B) + tau written (4 B)
 # DRAM bytes of one tau-kernel launch per skewer, from the ncu captures in
 # profiles/ (8,192 skewers of the Gpc workload; 262,144 rows of the grid),
-# scaled by the number of skewers.  Valid only for the kernel source they were
-# taken on: reported as null once paper_1105_4747_gb300/csrc/tau_extract.cu
-# changes.
-TAU_DRAM_BYTES_PER_SKEWER = {"gpc": (402.725632e6 + 76.099328e6) / 8192,
-                             "grid1536": (4.832250e9 + 1.551512e9) / 262144}
-TAU_PROFILED_SOURCE_SHA1 = "baa23b9688d05ea3c8c3be43ac9154216f7b199f"
+# scaled by the number of skewers, with the SHA-1 of the kernel source each
+# was taken on: reported as null once paper_1105_4747_gb300/csrc/tau_extract.cu
+# differs from it.
+TAU_DRAM_PROFILE = {"gpc": ((402.720512e6 + 76.045056e6) / 8192, "0476ec601baaed7a36ecedebcd4a657d3c15381e"),
+                    "grid1536": ((4.832250e9 + 1.551512e9) / 262144, "baa23b9688d05ea3c8c3be43ac9154216f7b199f")}
 
 
 def workload_config(spec, S, extra=None, grid=False):
@@ -431,10 +430,11 @@ def run_ours(args):
     achieved = ALG_BYTES_PER_PX * n_px / (tau_ms / 1e3) / 1e9
     import hashlib
     src = os.path.join(ROOT, "paper_1105_4747_gb300", "csrc", "tau_extract.cu")
-    same_kernel = hashlib.sha1(open(src, "rb").read()).hexdigest() == TAU_PROFILED_SOURCE_SHA1
+    per_skewer, profiled_sha = TAU_DRAM_PROFILE[args.workload]
+    same_kernel = hashlib.sha1(open(src, "rb").read()).hexdigest() == profiled_sha
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak,
-                "traffic": TAU_DRAM_BYTES_PER_SKEWER[args.workload] * S if same_kernel else None,
+                "traffic": per_skewer * S if same_kernel else None,
                 "kernel": "tau_tile_kernel<compensated,8>", "kernel_ms": tau_ms,
                 "peak_source": "measured" if peaks else "fallback",
                 "alg_bytes_per_launch": ALG_BYTES_PER_PX * n_px}

@@ -1,13 +1,15 @@
 // tau_extract.cu -- optical depth along skewers (Eq. 4-6), sm_103a.
 //
-// One CTA owns one skewer.  Two kernels:
-//   * tau_tile_kernel (FP32, the product path): sources counting-sorted by
-//     target pixel; four lanes share an eight-pixel tile, taken in order of
-//     candidate count, and sum the sources whose reach covers the tile
-//     (compensated or plain);
-//   * tau_kernel (FP64 comparator): sources counting-sorted by target pixel,
-//     then each output pixel sums the sources of the bins within the
-//     skewer's widest reach.
+// Three kernels:
+//   * tau_tile_kernel (FP32, the product path): one CTA per skewer; sources
+//     counting-sorted by target pixel; four lanes share an eight-pixel tile,
+//     taken in order of candidate count, and sum the sources whose reach
+//     covers the tile (compensated or plain);
+//   * tau_serve_kernel (the serving loop): the same per-skewer body run by
+//     1 to 8 warp groups of a persistent 1024-thread CTA over a work list;
+//   * tau_kernel (FP64 comparator): one CTA per skewer; sources
+//     counting-sorted by target pixel, then each output pixel sums the
+//     sources of the bins within the skewer's widest reach.
 //
 // Source j lands at the target pixel t_j = j + s_j (mod N), s_j = rint(v_j/du),
 // the pixel nearest u_j = v_H(j) + v_pec(j).  Velocity differences are formed
