@@ -13,6 +13,8 @@ Functions follow Greig, Bolton & Wyithe (2011):
   * :func:`flux_stats`   -- <F>, Var F, tau_eff = -ln<F>, 21-bin PDF (Sec. 5.2)
   * :func:`pdf_bin`      -- the PDF bin of one value (Sec. 5.2)
 plus the unit helpers (H(z), pixel widths, nbar_H, b(T), n_HI) they use.
+The mock-spectrum processing of Sec. 4 and the 1D flux power spectrum of
+Sec. 5.3 are in :mod:`oracle.mock` (FP64 numpy).
 """
 from __future__ import annotations
 
