@@ -226,6 +226,58 @@ lya_status lya_flux_at(const float* tau, int64_t n, double A, float* flux_out, v
 lya_status lya_flux_stats(const float* flux, int64_t n, lya_flux_stats_t* out,
                           void* stream);
 
+/*
+ * Pixel velocity width du (km/s) of a field's skewers: the Hubble-law width
+ * H(z) L / (h (1 + z) N) of Sec. 2.3 (Eq. 6 text).
+ */
+lya_status lya_field_pixel_width(lya_field field, double* du_kms);
+
+/*
+ * Mock spectra (Sec. 4): the transmitted flux of each skewer processed to look
+ * like an instrument's spectra.  The paper describes the steps in words; this
+ * library reads them as:
+ *   - instrument profile: periodic discrete convolution with the Gaussian
+ *     exp(-(m du)^2 / 2 sigma^2), sigma = FWHM / (2 sqrt(2 ln 2)), over
+ *     |m du| <= nsigma sigma, weights normalised to one (fwhm_kms = 0: none);
+ *   - resampling: input pixel i is the cell [(i - 1/2) du, (i + 1/2) du) of the
+ *     periodic skewer; output pixel k the cell [(k - 1/2) B, (k + 1/2) B),
+ *     B = bin_kms (<= 0: du), valued by the cell-overlap mean;
+ *   - path cut: floor(min(N du, max_kms) / B) output pixels (max_kms <= 0:
+ *     the whole skewer), e.g. the Ly-alpha to Ly-beta path less 3000 km/s;
+ *   - noise: (1/snr) g with g standard normal, Box-Muller on Philox4x32-10
+ *     (Salmon et al. 2011) with key = seed and counter = (output pixel,
+ *     row0 + skewer row, 0, 0) (snr = 0: none).
+ * flux: device [n_skewers][n_pix]; out: device [n_skewers][n_out] with n_out
+ * from lya_mock_shape.  LYA_EINVAL if 2W + 1 > n_pix for the profile's
+ * half-width W pixels, or the skewer does not fit shared memory (n_pix up to
+ * ~28,000).  Asynchronous on the stream.
+ */
+typedef struct {
+    double fwhm_kms;     /* instrument FWHM, km/s (0: no profile)                 */
+    double bin_kms;      /* output pixel width, km/s (<= 0: the input width)      */
+    double snr;          /* S/N per output pixel (0: no noise)                    */
+    double max_kms;      /* keep the first max_kms of each skewer (<= 0: all)     */
+    double nsigma;       /* profile window half-width in sigma (e.g. 6)          */
+    uint64_t seed;       /* noise key                                             */
+    int64_t row0;        /* noise counter of the first skewer of the call         */
+} lya_mock_params;
+
+lya_status lya_mock_shape(int64_t n_pix, double du_kms, const lya_mock_params* params, int64_t* n_out);
+lya_status lya_mock_spectra(const float* flux, int64_t n_skewers, int64_t n_pix, double du_kms,
+                            const lya_mock_params* params, float* out, void* stream);
+
+/*
+ * Line-of-sight flux power spectrum (Sec. 5.3): with delta_F = F / <F> - 1
+ * (<F> over every given pixel), P(k_n) = (du / N) |sum_j delta_j e^{-2 pi i j n / N}|^2
+ * averaged over the skewers, k_n = 2 pi n / (N du) s/km, n = 0 .. N/2.
+ * flux: device [n_skewers][n_pix] with n_pix = 2^a 3^b; k_out (nullable) and
+ * power_out: host arrays of n_pix/2 + 1; mean_flux_out (nullable): <F>.
+ * The transforms run in FP32 (two real skewers per complex transform); the
+ * sums over skewers in FP64.  Synchronises the stream.
+ */
+lya_status lya_flux_power_1d(const float* flux, int64_t n_skewers, int64_t n_pix, double du_kms,
+                             double* k_out, double* power_out, double* mean_flux_out, void* stream);
+
 /* ======================================================================
  * Serving: a persistent request loop over resident fields.
  *

@@ -20,7 +20,8 @@ gives these steps in words; the definitions below are the readings taken:
   * path cut: the first floor(min(V, L_cut) / B) output pixels, V = N du;
   * noise: sigma_n = 1 / (S/N) (continuum units) times a standard normal
     deviate, drawn by Box-Muller from Philox4x32-10 (Salmon et al. 2011) with
-    key = the 64-bit seed and counter = (output pixel, skewer row, 0, 0);
+    key = the 64-bit seed and counter = (output pixel, skewer row, 0, 0); the
+    uniforms are u = (top 24 bits of a word + 1/2) 2^-24, exact in FP32;
   * power spectrum: delta_F = F / <F> - 1 with <F> over every pixel given,
     P(k_n) = (du / N) |sum_j delta_j exp(-2 pi i j n / N)|^2 averaged over
     skewers, k_n = 2 pi n / (N du), n = 0 .. N/2 (s/km and km/s).
@@ -74,13 +75,13 @@ def philox4x32_10(c0, c1, c2, c3, k0: int, k1: int):
 
 def normal_deviates(seed: int, rows, n_cols: int) -> np.ndarray:
     """Standard normal deviates [len(rows)][n_cols]: Box-Muller on the first two
-    Philox words of counter (column, row low, row high, 0)."""
+    Philox words of counter (column, row low, row high, 0), 24-bit uniforms."""
     rows = np.asarray(rows, dtype=np.int64).ravel()
     kk, rr = np.meshgrid(np.arange(n_cols, dtype=np.uint64), rows.astype(np.uint64), indexing="xy")
     x = philox4x32_10(kk, rr & _LO, rr >> np.uint64(32), np.zeros_like(kk), seed & 0xFFFFFFFF,
                       (seed >> 32) & 0xFFFFFFFF)
-    u1 = (x[0].astype(np.float64) + 0.5) * 2.0 ** -32          # in (0, 1)
-    u2 = (x[1].astype(np.float64) + 0.5) * 2.0 ** -32
+    u1 = ((x[0] >> np.uint32(8)).astype(np.float64) + 0.5) * 2.0 ** -24     # in (0, 1)
+    u2 = ((x[1] >> np.uint32(8)).astype(np.float64) + 0.5) * 2.0 ** -24
     return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
 
 

@@ -16,9 +16,14 @@ from ._binding import (  # noqa: F401
     Field,
     FluxStats,
     LyaError,
+    MockParams,
     Server,
     ServerResult,
     extract_skewers,
+    field_pixel_width,
+    flux_power_1d,
+    mock_shape,
+    mock_spectra,
     flux_at,
     flux_stats,
     mean_flux_sums,

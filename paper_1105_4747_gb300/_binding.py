@@ -54,6 +54,12 @@ class _FluxStats(ctypes.Structure):
                 ("tau_eff", ctypes.c_double), ("pdf", ctypes.c_int64 * 21), ("n", ctypes.c_int64)]
 
 
+class _MockParams(ctypes.Structure):
+    _fields_ = [("fwhm_kms", ctypes.c_double), ("bin_kms", ctypes.c_double), ("snr", ctypes.c_double),
+                ("max_kms", ctypes.c_double), ("nsigma", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("row0", ctypes.c_int64)]
+
+
 class _ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int),
                 ("step_target_us", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int)]
@@ -114,6 +120,10 @@ def load_library():
         lib.lya_mean_flux_sums.argtypes = [vp, i64, d, ctypes.POINTER(d), vp]
         lib.lya_flux_at.argtypes = [vp, i64, d, vp, vp]
         u64 = ctypes.c_uint64
+        lib.lya_field_pixel_width.argtypes = [vp, ctypes.POINTER(d)]
+        lib.lya_mock_shape.argtypes = [i64, d, ctypes.POINTER(_MockParams), ctypes.POINTER(i64)]
+        lib.lya_mock_spectra.argtypes = [vp, i64, i64, d, ctypes.POINTER(_MockParams), vp, vp]
+        lib.lya_flux_power_1d.argtypes = [vp, i64, i64, d, vp, vp, ctypes.POINTER(d), vp]
         lib.lya_server_create.argtypes = [ctypes.POINTER(_ServerConfig), ctypes.POINTER(vp)]
         lib.lya_server_autotune.argtypes = [vp, vp, ctypes.POINTER(_ExtractParams), i64, ctypes.POINTER(i32)]
         lib.lya_server_submit.argtypes = [vp, vp, ctypes.POINTER(_ExtractParams), vp, i64, d, ctypes.POINTER(u64)]
@@ -128,7 +138,8 @@ def load_library():
                      "lya_rescale_mean_flux_noalloc", "lya_rescale_mean_flux_stats", "lya_flux_stats", "lya_tau_moments",
                      "lya_mean_flux_sums", "lya_flux_at", "lya_server_create", "lya_server_autotune",
                      "lya_server_submit", "lya_server_poll", "lya_server_wait", "lya_server_copy_flux",
-                     "lya_server_release", "lya_server_info", "lya_server_destroy"):
+                     "lya_server_release", "lya_server_info", "lya_server_destroy", "lya_field_pixel_width",
+                     "lya_mock_shape", "lya_mock_spectra", "lya_flux_power_1d"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -509,3 +520,67 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+@dataclass
+class MockParams:
+    """Instrument processing of mock spectra (Sec. 4); see lya_mock_params in include/lya.h."""
+    fwhm_kms: float = 0.0
+    bin_kms: float = 0.0
+    snr: float = 0.0
+    max_kms: float = 0.0
+    nsigma: float = 6.0
+    seed: int = 0
+    row0: int = 0
+
+    def _c(self) -> _MockParams:
+        return _MockParams(float(self.fwhm_kms), float(self.bin_kms), float(self.snr), float(self.max_kms),
+                           float(self.nsigma), int(self.seed) & 0xFFFFFFFFFFFFFFFF, int(self.row0))
+
+
+def field_pixel_width(field: Field) -> float:
+    """Pixel velocity width of the field's skewers, km/s (lya_field_pixel_width)."""
+    du = ctypes.c_double()
+    _check(load_library().lya_field_pixel_width(field.handle, ctypes.byref(du)), "lya_field_pixel_width")
+    return du.value
+
+
+def mock_shape(n_pix: int, du_kms: float, params: MockParams) -> int:
+    n = ctypes.c_int64()
+    p = params._c()
+    _check(load_library().lya_mock_shape(int(n_pix), float(du_kms), ctypes.byref(p), ctypes.byref(n)),
+           "lya_mock_shape")
+    return n.value
+
+
+def mock_spectra(flux, du_kms: float, params: MockParams, out=None, stream=None):
+    """Mock spectra [n_skewers][n_out] on the device (lya_mock_spectra)."""
+    torch = _torch()
+    _require_cuda_f32(flux, "flux")
+    if flux.dim() != 2:
+        raise ValueError("flux must be [n_skewers][n_pix]")
+    S, N = flux.shape
+    M = mock_shape(N, du_kms, params)
+    if out is None:
+        out = torch.empty((S, M), dtype=torch.float32, device=flux.device)
+    _require_cuda_f32(out, "out")
+    if out.numel() != S * M:
+        raise ValueError("out has the wrong size")
+    p = params._c()
+    _check(load_library().lya_mock_spectra(flux.data_ptr(), S, N, float(du_kms), ctypes.byref(p), out.data_ptr(),
+                                           _stream_handle(stream)), "lya_mock_spectra")
+    return out
+
+
+def flux_power_1d(flux, du_kms: float, stream=None):
+    """(k [s/km], P(k) [km/s], <F>) of the line-of-sight flux contrast (lya_flux_power_1d)."""
+    _require_cuda_f32(flux, "flux")
+    if flux.dim() != 2:
+        raise ValueError("flux must be [n_skewers][n_pix]")
+    S, N = flux.shape
+    k = np.empty(N // 2 + 1)
+    P = np.empty(N // 2 + 1)
+    mean = ctypes.c_double()
+    _check(load_library().lya_flux_power_1d(flux.data_ptr(), S, N, float(du_kms), k.ctypes.data, P.ctypes.data,
+                                            ctypes.byref(mean), _stream_handle(stream)), "lya_flux_power_1d")
+    return k, P, mean.value

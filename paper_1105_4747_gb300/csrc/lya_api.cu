@@ -367,6 +367,104 @@ lya_status lya_flux_at(const float* tau, int64_t n, double A, float* flux_out, v
     return lya::flux_at_run(tau, n, A, flux_out, static_cast<cudaStream_t>(stream));
 }
 
+lya_status lya_field_pixel_width(lya_field f, double* du_kms)
+{
+    if (!f || !du_kms) return LYA_EINVAL;
+    *du_kms = physics(f->desc, 1.0).du;
+    return LYA_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+struct MockPlan {
+    int W, M;
+    double du_over_sigma, ratio;
+};
+
+lya_status mock_plan(int64_t n_pix, double du, const lya_mock_params* p, MockPlan* out)
+{
+    if (!p || n_pix < 2 || n_pix > (1 << 24) || !(du > 0.0) || !std::isfinite(du)) return LYA_EINVAL;
+    if (!(p->fwhm_kms >= 0.0) || !(p->bin_kms >= 0.0) || !(p->snr >= 0.0) || !(p->max_kms >= 0.0)) return LYA_EINVAL;
+    if (!std::isfinite(p->fwhm_kms) || !std::isfinite(p->bin_kms) || !std::isfinite(p->snr) ||
+        !std::isfinite(p->max_kms))
+        return LYA_EINVAL;
+    MockPlan m{};
+    if (p->fwhm_kms > 0.0) {
+        if (!(p->nsigma > 0.0 && p->nsigma <= 40.0)) return LYA_EINVAL;
+        const double sigma = p->fwhm_kms / (2.0 * std::sqrt(2.0 * std::log(2.0)));
+        const double w = std::floor(p->nsigma * sigma / du);
+        if (2.0 * w + 1.0 > (double)n_pix) return LYA_EINVAL;    // the profile would wrap onto itself
+        m.W = (int)w;
+        m.du_over_sigma = du / sigma;
+    }
+    const double B = p->bin_kms > 0.0 ? p->bin_kms : du;
+    const double V = (double)n_pix * du;
+    const double L = p->max_kms > 0.0 ? std::fmin(V, p->max_kms) : V;
+    const double M = std::floor(L / B * (1.0 + 1e-12));
+    if (!(M >= 1.0) || M > (double)(1 << 24)) return LYA_EINVAL;
+    m.M = (int)M;
+    m.ratio = B / du;
+    *out = m;
+    return LYA_OK;
+}
+
+bool two_three_smooth(int64_t n)
+{
+    if (n < 2) return false;
+    while (n % 3 == 0) n /= 3;
+    while (n % 2 == 0) n /= 2;
+    return n == 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+lya_status lya_mock_shape(int64_t n_pix, double du_kms, const lya_mock_params* p, int64_t* n_out)
+{
+    if (!n_out) return LYA_EINVAL;
+    MockPlan m;
+    const lya_status st = mock_plan(n_pix, du_kms, p, &m);
+    if (st == LYA_OK) *n_out = m.M;
+    return st;
+}
+
+lya_status lya_mock_spectra(const float* flux, int64_t n_skewers, int64_t n_pix, double du_kms,
+                            const lya_mock_params* p, float* out, void* stream)
+{
+    if (!flux || !out || n_skewers < 1 || n_skewers > 0x7fffffffLL) return LYA_EINVAL;
+    MockPlan m;
+    const lya_status st = mock_plan(n_pix, du_kms, p, &m);
+    if (st != LYA_OK) return st;
+    if (lya::mock_smem_bytes((int)n_pix, m.W) > lya::max_dynamic_smem()) return LYA_EINVAL;
+    return lya::mock_spectra_run(flux, n_skewers, (int)n_pix, m.M, m.W, m.du_over_sigma, m.ratio,
+                                 p->snr > 0.0 ? 1.0 / p->snr : 0.0, p->seed, p->row0, out,
+                                 static_cast<cudaStream_t>(stream));
+}
+
+lya_status lya_flux_power_1d(const float* flux, int64_t n_skewers, int64_t n_pix, double du_kms,
+                             double* k_out, double* power_out, double* mean_flux_out, void* stream)
+{
+    if (!flux || !power_out || n_skewers < 1 || !(du_kms > 0.0) || !std::isfinite(du_kms)) return LYA_EINVAL;
+    if (!two_three_smooth(n_pix) || n_pix > 65536) return LYA_EINVAL;
+    if (lya::flux_ps_smem_bytes((int)n_pix) > lya::max_dynamic_smem()) return LYA_EINVAL;
+    const int H = (int)(n_pix / 2 + 1);
+    double mean = 0.0;
+    const lya_status st = lya::flux_power_run(flux, n_skewers, (int)n_pix, power_out, &mean,
+                                              static_cast<cudaStream_t>(stream));
+    if (st != LYA_OK) return st;
+    if (!(mean > 0.0)) return LYA_EINVAL;                 // no transmitted flux: delta_F undefined
+    const double norm = du_kms / (double)n_pix / (double)n_skewers;
+    for (int n = 0; n < H; ++n) {
+        power_out[n] *= norm;
+        if (k_out) k_out[n] = 2.0 * 3.14159265358979323846 * n / ((double)n_pix * du_kms);
+    }
+    if (mean_flux_out) *mean_flux_out = mean;
+    return LYA_OK;
+}
+
 lya_status lya_flux_stats(const float* flux, int64_t n, lya_flux_stats_t* out, void* stream)
 {
     if (!flux || n <= 0 || !out) return LYA_EINVAL;

@@ -93,6 +93,21 @@ lya_status flux_at_run(const float* tau, int64_t n, double A, float* flux, cudaS
 lya_status flux_stats_run(const float* flux, int64_t n, lya_flux_stats_t* out,
                           cudaStream_t stream);
 
+// Mock spectra (Sec. 4): instrument profile of half-width W pixels (0: none,
+// sigma = du / du_over_sigma), resampling to pixels ratio times wider, n_out
+// output pixels, noise sigma (0: none) from Philox keyed by seed, rows
+// counted from row0.
+lya_status mock_spectra_run(const float* flux, int64_t n_skewers, int n_pix, int n_out, int W,
+                            double du_over_sigma, double ratio, double noise, uint64_t seed,
+                            int64_t row0, float* out, cudaStream_t stream);
+size_t mock_smem_bytes(int n_pix, int W);
+
+// Line-of-sight flux power (Sec. 5.3): sums over skewers of |X_n|^2 of
+// delta_F = F/<F> - 1, n = 0..N/2 (host), and <F>.  n_pix = 2^a 3^b.
+lya_status flux_power_run(const float* flux, int64_t n_skewers, int n_pix, double* sums_out,
+                          double* mean_out, cudaStream_t stream);
+size_t flux_ps_smem_bytes(int n_pix);
+
 // Field validation: counts out-of-domain values and finds the largest T.
 struct FieldCheck {
     unsigned long long bad_rho, bad_vpec, bad_temp;

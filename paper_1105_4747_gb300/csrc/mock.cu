@@ -1,0 +1,352 @@
+// mock.cu -- mock spectra (Sec. 4) and the line-of-sight flux power spectrum
+// (Sec. 5.3) on sm_103a.
+//
+// mock_kernel: one CTA per skewer.  The skewer's F is staged in shared
+// memory; the instrument profile is a periodic discrete convolution with
+// normalised Gaussian weights (computed once per call in FP64 by
+// mock_weights_kernel); output pixel k of width B takes the cell-overlap mean
+// of the convolved input cells (cell edges in FP64, the sums in FP32); noise
+// of sigma 1/(S/N) comes from Philox4x32-10 (Salmon et al. 2011) keyed by the
+// seed and countered by (output pixel, skewer row), by Box-Muller on two
+// 24-bit uniforms.
+//
+// flux_ps_kernel: persistent CTAs over pairs of skewers.  Two real skewers
+// ride in one complex FFT (a + i b) of length N = 2^p 3^q, a Stockham
+// autosort decimation-in-frequency transform in shared memory (radix 3, then
+// radix 2 passes, twiddles from sincospi); the two spectra are separated by
+// conjugate symmetry and |X|^2 is summed per CTA, then once per CTA into the
+// FP64 totals.
+#include <cmath>
+#include <cstdint>
+
+#include "lya_device.cuh"
+#include "lya_internal.h"
+#include "mean_flux_device.cuh"
+
+namespace lya {
+namespace {
+
+using namespace mfd;
+
+constexpr int kMockThreads = 256;
+constexpr int kPsThreads = 512;
+
+// ---- Philox4x32-10 -------------------------------------------------------------------
+struct U4 { unsigned int x, y, z, w; };
+
+__device__ __forceinline__ U4 philox4x32_10(U4 c, unsigned int k0, unsigned int k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned int lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const unsigned int lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// A standard normal deviate for (column, row): Box-Muller on the first two
+// words, uniforms (w >> 8 + 1/2) 2^-24 (exact in FP32).
+__device__ __forceinline__ float normal_deviate(unsigned long long seed, long long col, long long row)
+{
+    const U4 r = philox4x32_10(U4{(unsigned int)col, (unsigned int)row, (unsigned int)((unsigned long long)row >> 32), 0u},
+                               (unsigned int)seed, (unsigned int)(seed >> 32));
+    const float u1 = ((float)(r.x >> 8) + 0.5f) * 5.9604644775390625e-8f;   // 2^-24
+    const float u2 = ((float)(r.y >> 8) + 0.5f) * 5.9604644775390625e-8f;
+    return sqrtf(-2.f * logf(u1)) * cospif(2.f * u2);
+}
+
+// ---- instrument profile weights (FP64, normalised) -----------------------------------
+__global__ void __launch_bounds__(kMockThreads) mock_weights_kernel(int W, double du_over_sigma, float* w)
+{
+    __shared__ double sh[1][32];
+    double s[1] = {0.0};
+    for (int m = -W + (int)threadIdx.x; m <= W; m += blockDim.x) {
+        const double x = m * du_over_sigma;
+        s[0] += exp(-0.5 * x * x);
+    }
+    block_sum<1>(s, sh);
+    __shared__ double total;
+    if (threadIdx.x == 0) total = s[0];
+    __syncthreads();
+    for (int m = -W + (int)threadIdx.x; m <= W; m += blockDim.x) {
+        const double x = m * du_over_sigma;
+        w[m + W] = (float)(exp(-0.5 * x * x) / total);
+    }
+}
+
+struct MockLaunch {
+    const float* flux;
+    float* out;
+    long long n_skewers;
+    int N, M, W;                 // input pixels, output pixels, profile half-width (0: none)
+    const float* w;              // 2W + 1 weights
+    double ratio;                // output pixel width / input pixel width
+    float noise;                 // sigma of the noise (0: none)
+    unsigned long long seed;
+    long long row0;              // noise counter of row 0
+};
+
+__global__ void __launch_bounds__(kMockThreads) mock_kernel(const MockLaunch L)
+{
+    extern __shared__ __align__(16) float sm[];
+    const int N = L.N, W = L.W;
+    float* in = sm;                                  // N
+    float* conv = W > 0 ? sm + N : sm;               // N (the input itself without a profile)
+    float* w = sm + (W > 0 ? 2 * N : N);             // 2W + 1
+    const long long row = blockIdx.x;
+    const float* F = L.flux + row * (long long)N;
+    if ((N & 3) == 0 && (reinterpret_cast<uintptr_t>(F) & 15) == 0) {
+        for (int k = threadIdx.x; 4 * k < N; k += blockDim.x)
+            reinterpret_cast<float4*>(in)[k] = __ldcs(reinterpret_cast<const float4*>(F) + k);
+    } else {
+        for (int i = threadIdx.x; i < N; i += blockDim.x) in[i] = __ldcs(F + i);
+    }
+    for (int m = threadIdx.x; m < 2 * W + 1 && W > 0; m += blockDim.x) w[m] = L.w[m];
+    __syncthreads();
+
+    // instrument profile: conv[i] = sum_m w[m] in[(i + m) mod N]
+    if (W > 0) {
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            float a0 = 0.f, a1 = 0.f;
+            int j = i - W;
+            if (j < 0) j += N;
+            int m = 0;
+            for (; m + 1 < 2 * W + 1; m += 2) {
+                a0 = fmaf(w[m], in[j], a0);
+                if (++j == N) j = 0;
+                a1 = fmaf(w[m + 1], in[j], a1);
+                if (++j == N) j = 0;
+            }
+            if (m < 2 * W + 1) a0 = fmaf(w[m], in[j], a0);
+            conv[i] = a0 + a1;
+        }
+        __syncthreads();
+    }
+
+    // resampling onto cells of width ratio (input cell i spans [i, i + 1) here),
+    // then noise
+    float* out = L.out + row * (long long)L.M;
+    const double r = L.ratio;
+    for (int k = threadIdx.x; k < L.M; k += blockDim.x) {
+        const double a = (k - 0.5) * r + 0.5, b = (k + 0.5) * r + 0.5;
+        const long long i0 = (long long)floor(a), i1 = (long long)ceil(b) - 1;
+        float acc = 0.f;
+        for (long long i = i0; i <= i1; ++i) {
+            const float ov = (float)(fmin(b, (double)(i + 1)) - fmax(a, (double)i));
+            long long ii = i % N;
+            if (ii < 0) ii += N;
+            acc = fmaf(ov, conv[ii], acc);
+        }
+        float y = (float)(acc / r);
+        if (L.noise > 0.f) y = fmaf(L.noise, normal_deviate(L.seed, k, L.row0 + row), y);
+        out[k] = y;
+    }
+}
+
+// ---- 1D flux power spectrum ---------------------------------------------------------
+struct PsLaunch {
+    const float* flux;
+    long long n_skewers;
+    int N;
+    const double* sum;           // device: sum of every F value
+    double* power;               // device: N/2 + 1 totals of |X_n|^2 (n_skewers summed)
+};
+
+__global__ void __launch_bounds__(kThreads) ps_sum_kernel(const float* __restrict__ F, long long n, double* out,
+                                                        double* part, unsigned int* ticket)
+{
+    KahanF32 s;
+    stream_f32(F, n, [&](long long, float f) { s.add(f); });
+    __shared__ double sh[1][32];
+    double v[1] = {(double)s.value()};
+    block_sum<1>(v, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = v[0];
+    if (!last_block(ticket)) return;
+    double t[1] = {0.0};
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t[0] += part[b];
+    block_sum<1>(t, sh);
+    if (threadIdx.x == 0) {
+        *out = t[0];
+        *ticket = 0;
+    }
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// exp(-2 pi i p k / n)
+__device__ __forceinline__ float2 twiddle(int p, int k, int n)
+{
+    float s, c;
+    sincospif(-2.f * (float)((long long)p * k % n) / (float)n, &s, &c);
+    return make_float2(c, s);
+}
+
+// One Stockham pass of radix R on length-N data: x -> y, n the current
+// sub-length, s the current stride (n s = N).
+template <int R>
+__device__ __forceinline__ void stockham_pass(const float2* __restrict__ x, float2* __restrict__ y, int N, int n,
+                                              int s)
+{
+    const int m = n / R;
+    for (int t = threadIdx.x; t < N / R; t += blockDim.x) {
+        const int q = t % s, p = t / s;
+        float2 a[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) a[j] = x[q + s * (p + j * m)];
+        float2 c[R];
+        if constexpr (R == 2) {
+            c[0] = make_float2(a[0].x + a[1].x, a[0].y + a[1].y);
+            c[1] = make_float2(a[0].x - a[1].x, a[0].y - a[1].y);
+        } else {
+            // w3 = exp(-2 pi i / 3) = (-1/2, -sqrt(3)/2)
+            const float h = 0.86602540378443865f;
+            const float2 s12 = make_float2(a[1].x + a[2].x, a[1].y + a[2].y);
+            const float2 d12 = make_float2(a[1].x - a[2].x, a[1].y - a[2].y);
+            c[0] = make_float2(a[0].x + s12.x, a[0].y + s12.y);
+            const float2 mid = make_float2(a[0].x - 0.5f * s12.x, a[0].y - 0.5f * s12.y);
+            // -i h d12 = (h d12.y, -h d12.x)
+            c[1] = make_float2(mid.x + h * d12.y, mid.y - h * d12.x);
+            c[2] = make_float2(mid.x - h * d12.y, mid.y + h * d12.x);
+        }
+        y[q + s * (R * p)] = c[0];
+#pragma unroll
+        for (int k = 1; k < R; ++k) y[q + s * (R * p + k)] = cmul(c[k], twiddle(p, k, n));
+    }
+}
+
+__global__ void __launch_bounds__(kPsThreads) flux_ps_kernel(const PsLaunch L)
+{
+    extern __shared__ __align__(16) float2 buf[];
+    const int N = L.N, H = N / 2 + 1;
+    float2* X = buf;
+    float2* Y = buf + N;
+    float* acc = reinterpret_cast<float*>(buf + 2 * N);        // H partial powers
+    for (int n = threadIdx.x; n < H; n += blockDim.x) acc[n] = 0.f;
+    const float inv_mean = (float)((double)L.n_skewers * N / *L.sum);
+    const long long pairs = (L.n_skewers + 1) / 2;
+    for (long long pr = blockIdx.x; pr < pairs; pr += gridDim.x) {
+        const long long ra = 2 * pr, rb = 2 * pr + 1;
+        const float* Fa = L.flux + ra * (long long)N;
+        const float* Fb = rb < L.n_skewers ? L.flux + rb * (long long)N : nullptr;
+        __syncthreads();                                       // the previous pair is done with X, Y
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            const float da = fmaf(__ldcs(Fa + i), inv_mean, -1.f);
+            const float db = Fb ? fmaf(__ldcs(Fb + i), inv_mean, -1.f) : 0.f;
+            X[i] = make_float2(da, db);
+        }
+        __syncthreads();
+        float2* src = X;
+        float2* dst = Y;
+        int n = N, s = 1;
+        while (n % 3 == 0) {
+            stockham_pass<3>(src, dst, N, n, s);
+            __syncthreads();
+            n /= 3;
+            s *= 3;
+            float2* t = src; src = dst; dst = t;
+        }
+        while (n > 1) {
+            stockham_pass<2>(src, dst, N, n, s);
+            __syncthreads();
+            n /= 2;
+            s *= 2;
+            float2* t = src; src = dst; dst = t;
+        }
+        // Z = A + i B: A_n = (Z_n + conj Z_{N-n}) / 2, B_n = (Z_n - conj Z_{N-n}) / 2i
+        for (int k = threadIdx.x; k < H; k += blockDim.x) {
+            const float2 z = src[k], zc = src[k == 0 ? 0 : N - k];
+            const float ar = 0.5f * (z.x + zc.x), ai = 0.5f * (z.y - zc.y);
+            const float br = 0.5f * (z.y + zc.y), bi = -0.5f * (z.x - zc.x);
+            acc[k] += ar * ar + ai * ai + (Fb ? br * br + bi * bi : 0.f);
+        }
+    }
+    __syncthreads();
+    for (int n = threadIdx.x; n < H; n += blockDim.x)
+        if (acc[n] != 0.f) atomicAdd(L.power + n, (double)acc[n]);
+}
+
+}  // namespace
+
+// ---- host side -----------------------------------------------------------------------
+lya_status mock_spectra_run(const float* flux, int64_t n_skewers, int n_pix, int n_out, int W, double du_over_sigma,
+                            double ratio, double noise, uint64_t seed, int64_t row0, float* out, cudaStream_t stream)
+{
+    float* w = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (W > 0) {
+        e = cudaMallocAsync((void**)&w, sizeof(float) * (2 * W + 1), stream);
+        if (e == cudaSuccess) {
+            mock_weights_kernel<<<1, kMockThreads, 0, stream>>>(W, du_over_sigma, w);
+            count_launch();
+            e = cudaGetLastError();
+        }
+    }
+    const size_t smem = sizeof(float) * ((W > 0 ? 2 : 1) * (size_t)n_pix + (W > 0 ? 2 * W + 1 : 0));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(mock_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess && n_skewers > 0) {
+        MockLaunch L{flux, out, (long long)n_skewers, n_pix, n_out, W, w, ratio, (float)noise, seed, (long long)row0};
+        mock_kernel<<<(unsigned)n_skewers, kMockThreads, smem, stream>>>(L);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    if (w) cudaFreeAsync(w, stream);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LYA_ENOMEM : LYA_ECUDA;
+    return LYA_OK;
+}
+
+size_t mock_smem_bytes(int n_pix, int W)
+{
+    return sizeof(float) * ((W > 0 ? 2 : 1) * (size_t)n_pix + (W > 0 ? 2 * W + 1 : 0));
+}
+
+size_t flux_ps_smem_bytes(int n_pix) { return sizeof(float2) * 2 * (size_t)n_pix + sizeof(float) * (n_pix / 2 + 1); }
+
+lya_status flux_power_run(const float* flux, int64_t n_skewers, int n_pix, double* sums_out /* host: N/2+1 */,
+                          double* mean_out, cudaStream_t stream)
+{
+    const long long n = (long long)n_skewers * n_pix;
+    const int H = n_pix / 2 + 1;
+    const int grid_sum = (int)std::min<long long>((n + kThreads - 1) / kThreads, 8LL * sm_count());
+    double* d = nullptr;       // [0] sum of F, [1..H] power totals, then partials
+    unsigned int* ticket = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&d, sizeof(double) * (1 + H + grid_sum), stream);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&ticket, sizeof(unsigned int), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, sizeof(double) * (1 + H), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ticket, 0, sizeof(unsigned int), stream);
+    if (e == cudaSuccess) {
+        ps_sum_kernel<<<grid_sum, kThreads, 0, stream>>>(flux, n, d, d + 1 + H, ticket);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    const size_t smem = flux_ps_smem_bytes(n_pix);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(flux_ps_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, flux_ps_kernel, kPsThreads, smem);
+        const long long pairs = (n_skewers + 1) / 2;
+        const int grid = (int)std::min<long long>(pairs, (long long)std::max(per_sm, 1) * sm_count());
+        if (e == cudaSuccess) {
+            PsLaunch L{flux, (long long)n_skewers, n_pix, d, d + 1};
+            flux_ps_kernel<<<grid, kPsThreads, smem, stream>>>(L);
+            count_launch();
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sums_out, d + 1, sizeof(double) * H, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mean_out, d, sizeof(double), cudaMemcpyDeviceToHost, stream);
+    if (d) cudaFreeAsync(d, stream);
+    if (ticket) cudaFreeAsync(ticket, stream);
+    const cudaError_t e2 = cudaStreamSynchronize(stream);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LYA_ENOMEM : LYA_ECUDA;
+    *mean_out /= (double)n;
+    return LYA_OK;
+}
+
+}  // namespace lya
