@@ -333,6 +333,48 @@ def run_serving(lya, torch, warm_s, measure_s, burst=400, budget=SERVE_BUDGET):
                     "power law"}
 
 
+def run_post(lya, torch, field, F, S, spec, reps):
+    """Timings of lya_mock_spectra (the BOSS-like instrument of Sec. 4) and
+    lya_flux_power_1d on the step's F, with their HBM rooflines."""
+    c_kms = 2.99792458e5
+    du = lya.field_pixel_width(field)
+    p = lya.MockParams(fwhm_kms=224.0, bin_kms=c_kms * 1.0375 / (1215.67 * (1.0 + spec.z)), snr=5.0,
+                       max_kms=c_kms * np.log(1215.67 / 1025.72) - 3000.0, seed=11)
+    out = lya.mock_spectra(F, du, p)
+    M = out.shape[1]
+    lya.flux_power_1d(F, du)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record(stream)
+    for _ in range(reps):
+        lya.mock_spectra(F, du, p, out=out)
+    ev[1].record(stream)
+    ev[2].record(stream)
+    for _ in range(reps):
+        lya.flux_power_1d(F, du)
+    ev[3].record(stream)
+    ev[3].synchronize()
+    ms_mock = ev[0].elapsed_time(ev[1]) / reps
+    ms_ps = ev[2].elapsed_time(ev[3]) / reps
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    n_px = S * spec.n_pix
+    b_mock = 4 * n_px + 4 * S * M            # read F, write the mock pixels
+    b_ps = 8 * n_px                          # F read by the mean pass and by the transform pass
+    return {"mock_spectra": {"instrument": "FWHM 224 km/s, 1.0375 A pixels, S/N 5, Ly-alpha to Ly-beta path less "
+                                           "3000 km/s (Sec. 4)", "n_out_pix": M, "ms": ms_mock,
+                             "input_px_per_s": n_px / (ms_mock / 1e3),
+                             "roofline": {"bound": "hbm", "achieved": b_mock / (ms_mock / 1e3) / 1e9, "peak": peak,
+                                          "unit": "GB/s", "frac": b_mock / (ms_mock / 1e3) / 1e9 / peak,
+                                          "alg_bytes_per_launch": b_mock}},
+            "flux_power_1d": {"ms": ms_ps, "input_px_per_s": n_px / (ms_ps / 1e3),
+                              "roofline": {"bound": "hbm", "achieved": b_ps / (ms_ps / 1e3) / 1e9, "peak": peak,
+                                           "unit": "GB/s", "frac": b_ps / (ms_ps / 1e3) / 1e9 / peak,
+                                           "alg_bytes_per_launch": b_ps},
+                              "note": "includes the host round trip of the call (it synchronises)"}}
+
+
 def run_e2e(lya, torch, field, spec, S, params, target, rho, v, t, tau, F, n_steps, world, local):
     """Pipelined end-to-end steps through the public API (see run_ours)."""
     n_px = S * spec.n_pix
@@ -455,6 +497,12 @@ def run_ours(args):
     ms = max_over_ranks(ms, world)
     tau_ms = statistics.mean(a.elapsed_time(b) for a, b in tau_ev)
 
+    # the mock-spectrum processing (Sec. 4) and the 1D flux power spectrum
+    # (Sec. 5.3) on this step's F
+    post = None
+    if not grid and not args.no_post:
+        post = run_post(lya, torch, field, F, S, spec, args.steps)
+
     # end to end through the public API: host inputs in, host flux out.  Two
     # device fields and two F buffers let step k+1's inputs cross to the device
     # (a loader thread, lya_field_load on its own stream) and step k-1's F
@@ -497,7 +545,7 @@ def run_ours(args):
                 "config": workload_config(spec, S, {"parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                                                     "A": A, "mean_flux": st.mean_flux}, grid),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "serving": serving}
+                "clocks": clk, "serving": serving, "post": post}
         print(json.dumps(line), flush=True)
     field.close()
     if world > 1:
@@ -544,6 +592,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-post", action="store_true", help="skip the mock-spectrum and flux-power timings")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="measured seconds of the Poisson request stream in the default run")
     ap.add_argument("--serve-burst", type=int, default=400, help="requests of the capacity burst")

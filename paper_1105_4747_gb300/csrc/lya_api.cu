@@ -438,7 +438,7 @@ lya_status lya_mock_spectra(const float* flux, int64_t n_skewers, int64_t n_pix,
     MockPlan m;
     const lya_status st = mock_plan(n_pix, du_kms, p, &m);
     if (st != LYA_OK) return st;
-    if (lya::mock_smem_bytes((int)n_pix, m.W) > lya::max_dynamic_smem()) return LYA_EINVAL;
+    if (lya::mock_smem_bytes((int)n_pix, m.M, m.ratio, m.W) > lya::max_dynamic_smem()) return LYA_EINVAL;
     return lya::mock_spectra_run(flux, n_skewers, (int)n_pix, m.M, m.W, m.du_over_sigma, m.ratio,
                                  p->snr > 0.0 ? 1.0 / p->snr : 0.0, p->seed, p->row0, out,
                                  static_cast<cudaStream_t>(stream));

@@ -100,7 +100,7 @@ lya_status flux_stats_run(const float* flux, int64_t n, lya_flux_stats_t* out,
 lya_status mock_spectra_run(const float* flux, int64_t n_skewers, int n_pix, int n_out, int W,
                             double du_over_sigma, double ratio, double noise, uint64_t seed,
                             int64_t row0, float* out, cudaStream_t stream);
-size_t mock_smem_bytes(int n_pix, int W);
+size_t mock_smem_bytes(int n_pix, int n_out, double ratio, int W);
 
 // Line-of-sight flux power (Sec. 5.3): sums over skewers of |X_n|^2 of
 // delta_F = F/<F> - 1, n = 0..N/2 (host), and <F>.  n_pix = 2^a 3^b.

@@ -1,11 +1,12 @@
 // mock.cu -- mock spectra (Sec. 4) and the line-of-sight flux power spectrum
 // (Sec. 5.3) on sm_103a.
 //
-// mock_kernel: one CTA per skewer.  The skewer's F is staged in shared
-// memory; the instrument profile is a periodic discrete convolution with
-// normalised Gaussian weights (computed once per call in FP64 by
-// mock_weights_kernel); output pixel k of width B takes the cell-overlap mean
-// of the convolved input cells (cell edges in FP64, the sums in FP32); noise
+// mock_kernel: one CTA per skewer.  The input cells the output reads, with a
+// periodic halo of the profile's half-width, are staged in shared memory; the
+// instrument profile is a discrete convolution with normalised Gaussian
+// weights (computed once per call in FP64 by mock_weights_kernel), evaluated
+// only on those cells; output pixel k of width B takes the cell-overlap mean
+// of the convolved cells (cell edges in FP64, fractions and sums in FP32); noise
 // of sigma 1/(S/N) comes from Philox4x32-10 (Salmon et al. 2011) keyed by the
 // seed and countered by (output pixel, skewer row), by Box-Muller on two
 // 24-bit uniforms.
@@ -82,6 +83,7 @@ struct MockLaunch {
     float* out;
     long long n_skewers;
     int N, M, W;                 // input pixels, output pixels, profile half-width (0: none)
+    int i_lo, n_cells;           // the input cells the output reads: i_lo .. i_lo + n_cells - 1 (periodic)
     const float* w;              // 2W + 1 weights
     double ratio;                // output pixel width / input pixel width
     float noise;                 // sigma of the noise (0: none)
@@ -89,56 +91,62 @@ struct MockLaunch {
     long long row0;              // noise counter of row 0
 };
 
+// Shared memory: the cells i_lo - W .. i_lo + n_cells - 1 + W of the skewer
+// (periodic copies, so the profile needs no wrap test), the convolved cells,
+// the weights.
 __global__ void __launch_bounds__(kMockThreads) mock_kernel(const MockLaunch L)
 {
     extern __shared__ __align__(16) float sm[];
-    const int N = L.N, W = L.W;
-    float* in = sm;                                  // N
-    float* conv = W > 0 ? sm + N : sm;               // N (the input itself without a profile)
-    float* w = sm + (W > 0 ? 2 * N : N);             // 2W + 1
+    const int N = L.N, W = L.W, nc = L.n_cells;
+    const int n_ext = nc + 2 * W;
+    float* ext = sm;                                  // n_ext
+    float* conv = W > 0 ? sm + n_ext : sm;            // nc (the cells themselves without a profile)
+    float* w = sm + (W > 0 ? n_ext + nc : n_ext);     // 2W + 1
     const long long row = blockIdx.x;
     const float* F = L.flux + row * (long long)N;
-    if ((N & 3) == 0 && (reinterpret_cast<uintptr_t>(F) & 15) == 0) {
-        for (int k = threadIdx.x; 4 * k < N; k += blockDim.x)
-            reinterpret_cast<float4*>(in)[k] = __ldcs(reinterpret_cast<const float4*>(F) + k);
-    } else {
-        for (int i = threadIdx.x; i < N; i += blockDim.x) in[i] = __ldcs(F + i);
+    int src = (L.i_lo - W) % N;
+    if (src < 0) src += N;
+    for (int c = threadIdx.x; c < n_ext; c += blockDim.x) {
+        int i = src + c;
+        while (i >= N) i -= N;
+        ext[c] = __ldcs(F + i);
     }
     for (int m = threadIdx.x; m < 2 * W + 1 && W > 0; m += blockDim.x) w[m] = L.w[m];
     __syncthreads();
 
-    // instrument profile: conv[i] = sum_m w[m] in[(i + m) mod N]
+    // instrument profile: conv[c] = sum_m w[m] ext[c + m]
     if (W > 0) {
-        for (int i = threadIdx.x; i < N; i += blockDim.x) {
-            float a0 = 0.f, a1 = 0.f;
-            int j = i - W;
-            if (j < 0) j += N;
+        const int taps = 2 * W + 1;
+        for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+            const float* x = ext + c;
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
             int m = 0;
-            for (; m + 1 < 2 * W + 1; m += 2) {
-                a0 = fmaf(w[m], in[j], a0);
-                if (++j == N) j = 0;
-                a1 = fmaf(w[m + 1], in[j], a1);
-                if (++j == N) j = 0;
+            for (; m + 3 < taps; m += 4) {
+                a0 = fmaf(w[m], x[m], a0);
+                a1 = fmaf(w[m + 1], x[m + 1], a1);
+                a2 = fmaf(w[m + 2], x[m + 2], a2);
+                a3 = fmaf(w[m + 3], x[m + 3], a3);
             }
-            if (m < 2 * W + 1) a0 = fmaf(w[m], in[j], a0);
-            conv[i] = a0 + a1;
+            for (; m < taps; ++m) a0 = fmaf(w[m], x[m], a0);
+            conv[c] = (a0 + a1) + (a2 + a3);
         }
         __syncthreads();
     }
 
-    // resampling onto cells of width ratio (input cell i spans [i, i + 1) here),
-    // then noise
+    // resampling: output pixel k spans cells [a, b) (cell units relative to
+    // i_lo), edges in FP64, the overlap fractions and sums in FP32; then noise
     float* out = L.out + row * (long long)L.M;
     const double r = L.ratio;
     for (int k = threadIdx.x; k < L.M; k += blockDim.x) {
-        const double a = (k - 0.5) * r + 0.5, b = (k + 0.5) * r + 0.5;
-        const long long i0 = (long long)floor(a), i1 = (long long)ceil(b) - 1;
-        float acc = 0.f;
-        for (long long i = i0; i <= i1; ++i) {
-            const float ov = (float)(fmin(b, (double)(i + 1)) - fmax(a, (double)i));
-            long long ii = i % N;
-            if (ii < 0) ii += N;
-            acc = fmaf(ov, conv[ii], acc);
+        const double a = fma((double)k - 0.5, r, 0.5 - L.i_lo), b = fma((double)k + 0.5, r, 0.5 - L.i_lo);
+        const int ia = max((int)floor(a), 0), ib = min((int)ceil(b) - 1, L.n_cells - 1);
+        float acc;
+        if (ia == ib) {
+            acc = (float)(b - a) * conv[ia];
+        } else {
+            acc = (float)((double)(ia + 1) - a) * conv[ia];
+            for (int i = ia + 1; i < ib; ++i) acc += conv[i];
+            acc = fmaf((float)(b - (double)ib), conv[ib], acc);
         }
         float y = (float)(acc / r);
         if (L.noise > 0.f) y = fmaf(L.noise, normal_deviate(L.seed, k, L.row0 + row), y);
@@ -274,6 +282,26 @@ __global__ void __launch_bounds__(kPsThreads) flux_ps_kernel(const PsLaunch L)
 }  // namespace
 
 // ---- host side -----------------------------------------------------------------------
+// The input cells output pixels 0 .. M-1 read (cell units, i_lo may be
+// negative), with one spare cell on each side so that rounding of the FP64
+// edges on the device can never index outside them.
+static void mock_cells(int M, double ratio, int* i_lo, int* n_cells)
+{
+    const int lo = (int)std::floor(0.5 - 0.5 * ratio) - 1;
+    const int hi = (int)std::ceil((M - 0.5) * ratio + 0.5);
+    *i_lo = lo;
+    *n_cells = hi - lo + 1;
+}
+
+size_t mock_smem_bytes(int n_pix, int n_out, double ratio, int W)
+{
+    int lo, nc;
+    mock_cells(n_out, ratio, &lo, &nc);
+    (void)n_pix;
+    const size_t n_ext = (size_t)nc + 2 * (size_t)W;
+    return sizeof(float) * (n_ext + (W > 0 ? (size_t)nc + 2 * (size_t)W + 1 : 0));
+}
+
 lya_status mock_spectra_run(const float* flux, int64_t n_skewers, int n_pix, int n_out, int W, double du_over_sigma,
                             double ratio, double noise, uint64_t seed, int64_t row0, float* out, cudaStream_t stream)
 {
@@ -287,10 +315,13 @@ lya_status mock_spectra_run(const float* flux, int64_t n_skewers, int n_pix, int
             e = cudaGetLastError();
         }
     }
-    const size_t smem = sizeof(float) * ((W > 0 ? 2 : 1) * (size_t)n_pix + (W > 0 ? 2 * W + 1 : 0));
+    int i_lo, n_cells;
+    mock_cells(n_out, ratio, &i_lo, &n_cells);
+    const size_t smem = mock_smem_bytes(n_pix, n_out, ratio, W);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(mock_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess && n_skewers > 0) {
-        MockLaunch L{flux, out, (long long)n_skewers, n_pix, n_out, W, w, ratio, (float)noise, seed, (long long)row0};
+        MockLaunch L{flux, out, (long long)n_skewers, n_pix, n_out, W, i_lo, n_cells, w, ratio, (float)noise, seed,
+                     (long long)row0};
         mock_kernel<<<(unsigned)n_skewers, kMockThreads, smem, stream>>>(L);
         count_launch();
         e = cudaGetLastError();
@@ -298,11 +329,6 @@ lya_status mock_spectra_run(const float* flux, int64_t n_skewers, int n_pix, int
     if (w) cudaFreeAsync(w, stream);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LYA_ENOMEM : LYA_ECUDA;
     return LYA_OK;
-}
-
-size_t mock_smem_bytes(int n_pix, int W)
-{
-    return sizeof(float) * ((W > 0 ? 2 : 1) * (size_t)n_pix + (W > 0 ? 2 * W + 1 : 0));
 }
 
 size_t flux_ps_smem_bytes(int n_pix) { return sizeof(float2) * 2 * (size_t)n_pix + sizeof(float) * (n_pix / 2 + 1); }
