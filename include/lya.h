@@ -278,6 +278,34 @@ lya_status lya_mock_spectra(const float* flux, int64_t n_skewers, int64_t n_pix,
 lya_status lya_flux_power_1d(const float* flux, int64_t n_skewers, int64_t n_pix, double du_kms,
                              double* k_out, double* power_out, double* mean_flux_out, void* stream);
 
+/*
+ * Lines of sight generated in Fourier space on the device (Sec. 2.1-2.2),
+ * one independent 1D realisation per skewer id: modes k_n = 2 pi n / box,
+ * n = 1 .. N/2 - 1, with the 1D linear power P_n ~ k_n^-1 exp(-(k_n/k_j)^2)
+ * normalised to sum_n P_n = sigma_delta^2; amplitudes (N/2) sqrt(P_n)
+ * conj(g_n), g_n = a + i b with a, b standard normal (Box-Muller on
+ * Philox4x32-10, key = seed, counter = (n, id)); the Eq. 3 velocity
+ * i aH delta_n / k_n (f = 1); the Eq. 1 gas smoothing 1/(1 + k^2/k_f^2) of the
+ * density (k_f = 0: none); and the lognormal 1 + delta = exp(delta_b -
+ * sigma_b^2/2), sigma_b^2 = sum_n P_n/(1 + k_n^2/k_f^2)^2, in place of the
+ * paper's rank-ordered mapping to a hydrodynamical simulation.  Rows
+ * first_id .. first_id + n_ids - 1 are written to rho_out and vpec_out
+ * (device, [n_ids][n_pix] each); any subset of ids reproduces the same rows.
+ * n_pix = 2^a 3^b with a >= 1 (up to 9,216 by shared memory).  The transform
+ * runs in FP32.  Asynchronous on the stream.
+ */
+typedef struct {
+    double box;          /* comoving skewer length, h^-1 Mpc                      */
+    double z, h, omega_m, omega_l;
+    double k_j;          /* power cut-off scale, h Mpc^-1                        */
+    double sigma_delta;  /* rms of the linear density contrast                   */
+    double k_f;          /* Eq. 1 filtering scale, h Mpc^-1 (0: none)           */
+    uint64_t seed;
+} lya_sightline_desc;
+
+lya_status lya_generate_sightlines(const lya_sightline_desc* desc, int64_t n_pix, int64_t first_id,
+                                   int64_t n_ids, float* rho_out, float* vpec_out, void* stream);
+
 /* ======================================================================
  * Serving: a persistent request loop over resident fields.
  *

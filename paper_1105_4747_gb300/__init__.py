@@ -22,6 +22,7 @@ from ._binding import (  # noqa: F401
     extract_skewers,
     field_pixel_width,
     flux_power_1d,
+    generate_sightlines,
     mock_shape,
     mock_spectra,
     flux_at,

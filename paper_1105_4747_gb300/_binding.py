@@ -60,6 +60,12 @@ class _MockParams(ctypes.Structure):
                 ("row0", ctypes.c_int64)]
 
 
+class _SightlineDesc(ctypes.Structure):
+    _fields_ = [("box", ctypes.c_double), ("z", ctypes.c_double), ("h", ctypes.c_double),
+                ("omega_m", ctypes.c_double), ("omega_l", ctypes.c_double), ("k_j", ctypes.c_double),
+                ("sigma_delta", ctypes.c_double), ("k_f", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
 class _ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int),
                 ("step_target_us", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int)]
@@ -121,6 +127,7 @@ def load_library():
         lib.lya_flux_at.argtypes = [vp, i64, d, vp, vp]
         u64 = ctypes.c_uint64
         lib.lya_field_pixel_width.argtypes = [vp, ctypes.POINTER(d)]
+        lib.lya_generate_sightlines.argtypes = [ctypes.POINTER(_SightlineDesc), i64, i64, i64, vp, vp, vp]
         lib.lya_mock_shape.argtypes = [i64, d, ctypes.POINTER(_MockParams), ctypes.POINTER(i64)]
         lib.lya_mock_spectra.argtypes = [vp, i64, i64, d, ctypes.POINTER(_MockParams), vp, vp]
         lib.lya_flux_power_1d.argtypes = [vp, i64, i64, d, vp, vp, ctypes.POINTER(d), vp]
@@ -139,7 +146,7 @@ def load_library():
                      "lya_mean_flux_sums", "lya_flux_at", "lya_server_create", "lya_server_autotune",
                      "lya_server_submit", "lya_server_poll", "lya_server_wait", "lya_server_copy_flux",
                      "lya_server_release", "lya_server_info", "lya_server_destroy", "lya_field_pixel_width",
-                     "lya_mock_shape", "lya_mock_spectra", "lya_flux_power_1d"):
+                     "lya_mock_shape", "lya_mock_spectra", "lya_flux_power_1d", "lya_generate_sightlines"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -584,3 +591,24 @@ def flux_power_1d(flux, du_kms: float, stream=None):
     _check(load_library().lya_flux_power_1d(flux.data_ptr(), S, N, float(du_kms), k.ctypes.data, P.ctypes.data,
                                             ctypes.byref(mean), _stream_handle(stream)), "lya_flux_power_1d")
     return k, P, mean.value
+
+
+def generate_sightlines(n_pix: int, first_id: int, n_ids: int, *, box: float, z: float, k_j: float,
+                        sigma_delta: float, seed: int, k_f: float = 0.0, h: float = 0.72, omega_m: float = 0.26,
+                        omega_l: float = 0.74, rho_out=None, vpec_out=None, stream=None):
+    """(1 + delta, v_pec) [n_ids][n_pix] generated on the device (lya_generate_sightlines)."""
+    torch = _torch()
+    if rho_out is None:
+        rho_out = torch.empty((n_ids, n_pix), dtype=torch.float32, device="cuda")
+    if vpec_out is None:
+        vpec_out = torch.empty((n_ids, n_pix), dtype=torch.float32, device="cuda")
+    for t, name in ((rho_out, "rho_out"), (vpec_out, "vpec_out")):
+        _require_cuda_f32(t, name)
+        if t.numel() != n_ids * n_pix:
+            raise ValueError(f"{name} has the wrong size")
+    desc = _SightlineDesc(float(box), float(z), float(h), float(omega_m), float(omega_l), float(k_j),
+                          float(sigma_delta), float(k_f), int(seed) & 0xFFFFFFFFFFFFFFFF)
+    _check(load_library().lya_generate_sightlines(ctypes.byref(desc), int(n_pix), int(first_id), int(n_ids),
+                                                  rho_out.data_ptr(), vpec_out.data_ptr(), _stream_handle(stream)),
+           "lya_generate_sightlines")
+    return rho_out, vpec_out

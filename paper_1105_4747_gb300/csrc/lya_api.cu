@@ -465,6 +465,27 @@ lya_status lya_flux_power_1d(const float* flux, int64_t n_skewers, int64_t n_pix
     return LYA_OK;
 }
 
+lya_status lya_generate_sightlines(const lya_sightline_desc* d, int64_t n_pix, int64_t first_id, int64_t n_ids,
+                                   float* rho_out, float* vpec_out, void* stream)
+{
+    if (!d || n_ids < 0 || n_ids > 0x7fffffffLL || first_id < 0 || (n_ids > 0 && (!rho_out || !vpec_out)))
+        return LYA_EINVAL;
+    if (n_pix < 4 || (n_pix & 1) || !two_three_smooth(n_pix)) return LYA_EINVAL;
+    if (lya::sightline_smem_bytes((int)n_pix) > lya::max_dynamic_smem()) return LYA_EINVAL;
+    if (!(d->box > 0.0) || !(d->z > -1.0) || !(d->h > 0.0) || !(d->omega_m >= 0.0) || !(d->omega_l >= 0.0))
+        return LYA_EINVAL;
+    if (!(d->k_j > 0.0) || !(d->sigma_delta >= 0.0) || !(d->k_f >= 0.0)) return LYA_EINVAL;
+    if (!std::isfinite(d->box) || !std::isfinite(d->z) || !std::isfinite(d->k_j) || !std::isfinite(d->sigma_delta) ||
+        !std::isfinite(d->k_f))
+        return LYA_EINVAL;
+    const double zp = 1.0 + d->z;
+    const double e2 = d->omega_m * zp * zp * zp + d->omega_l;
+    if (!(e2 > 0.0)) return LYA_EINVAL;
+    const double aH = 100.0 * std::sqrt(e2) / zp;        // km/s per comoving h^-1 Mpc (h cancels)
+    return lya::sightlines_run((int)n_pix, d->box, d->k_j, d->sigma_delta, d->k_f, aH, d->seed, first_id, n_ids,
+                               rho_out, vpec_out, static_cast<cudaStream_t>(stream));
+}
+
 lya_status lya_flux_stats(const float* flux, int64_t n, lya_flux_stats_t* out, void* stream)
 {
     if (!flux || n <= 0 || !out) return LYA_EINVAL;

@@ -108,6 +108,13 @@ lya_status flux_power_run(const float* flux, int64_t n_skewers, int n_pix, doubl
                           double* mean_out, cudaStream_t stream);
 size_t flux_ps_smem_bytes(int n_pix);
 
+// Lines of sight generated in Fourier space (Sec. 2.1-2.2): rows
+// first_id .. first_id + n_ids - 1 of a field; n_pix = 2^a 3^b, a >= 1.
+lya_status sightlines_run(int n_pix, double box, double k_j, double sigma, double k_f, double aH,
+                          uint64_t seed, int64_t first_id, int64_t n_ids, float* rho, float* vpec,
+                          cudaStream_t stream);
+size_t sightline_smem_bytes(int n_pix);
+
 // Field validation: counts out-of-domain values and finds the largest T.
 struct FieldCheck {
     unsigned long long bad_rho, bad_vpec, bad_temp;

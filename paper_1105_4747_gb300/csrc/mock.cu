@@ -14,7 +14,7 @@
 // flux_ps_kernel: persistent CTAs over pairs of skewers.  Two real skewers
 // ride in one complex FFT (a + i b) of length N = 2^p 3^q, a Stockham
 // autosort decimation-in-frequency transform in shared memory (radix 3, then
-// radix 2 passes, twiddles from sincospi); the two spectra are separated by
+// radix 2 passes, twiddles from a per-CTA table); the two spectra are separated by
 // conjugate symmetry and |X|^2 is summed per CTA, then once per CTA into the
 // FP64 totals.
 #include <cmath>
@@ -23,41 +23,16 @@
 #include "lya_device.cuh"
 #include "lya_internal.h"
 #include "mean_flux_device.cuh"
+#include "fft_device.cuh"
 
 namespace lya {
 namespace {
 
 using namespace mfd;
+using namespace fftd;
 
 constexpr int kMockThreads = 256;
 constexpr int kPsThreads = 512;
-
-// ---- Philox4x32-10 -------------------------------------------------------------------
-struct U4 { unsigned int x, y, z, w; };
-
-__device__ __forceinline__ U4 philox4x32_10(U4 c, unsigned int k0, unsigned int k1)
-{
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const unsigned int lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const unsigned int lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    return c;
-}
-
-// A standard normal deviate for (column, row): Box-Muller on the first two
-// words, uniforms (w >> 8 + 1/2) 2^-24 (exact in FP32).
-__device__ __forceinline__ float normal_deviate(unsigned long long seed, long long col, long long row)
-{
-    const U4 r = philox4x32_10(U4{(unsigned int)col, (unsigned int)row, (unsigned int)((unsigned long long)row >> 32), 0u},
-                               (unsigned int)seed, (unsigned int)(seed >> 32));
-    const float u1 = ((float)(r.x >> 8) + 0.5f) * 5.9604644775390625e-8f;   // 2^-24
-    const float u2 = ((float)(r.y >> 8) + 0.5f) * 5.9604644775390625e-8f;
-    return sqrtf(-2.f * logf(u1)) * cospif(2.f * u2);
-}
 
 // ---- instrument profile weights (FP64, normalised) -----------------------------------
 __global__ void __launch_bounds__(kMockThreads) mock_weights_kernel(int W, double du_over_sigma, float* w)
@@ -182,60 +157,16 @@ __global__ void __launch_bounds__(kThreads) ps_sum_kernel(const float* __restric
     }
 }
 
-__device__ __forceinline__ float2 cmul(float2 a, float2 b)
-{
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-
-// exp(-2 pi i p k / n)
-__device__ __forceinline__ float2 twiddle(int p, int k, int n)
-{
-    float s, c;
-    sincospif(-2.f * (float)((long long)p * k % n) / (float)n, &s, &c);
-    return make_float2(c, s);
-}
-
-// One Stockham pass of radix R on length-N data: x -> y, n the current
-// sub-length, s the current stride (n s = N).
-template <int R>
-__device__ __forceinline__ void stockham_pass(const float2* __restrict__ x, float2* __restrict__ y, int N, int n,
-                                              int s)
-{
-    const int m = n / R;
-    for (int t = threadIdx.x; t < N / R; t += blockDim.x) {
-        const int q = t % s, p = t / s;
-        float2 a[R];
-#pragma unroll
-        for (int j = 0; j < R; ++j) a[j] = x[q + s * (p + j * m)];
-        float2 c[R];
-        if constexpr (R == 2) {
-            c[0] = make_float2(a[0].x + a[1].x, a[0].y + a[1].y);
-            c[1] = make_float2(a[0].x - a[1].x, a[0].y - a[1].y);
-        } else {
-            // w3 = exp(-2 pi i / 3) = (-1/2, -sqrt(3)/2)
-            const float h = 0.86602540378443865f;
-            const float2 s12 = make_float2(a[1].x + a[2].x, a[1].y + a[2].y);
-            const float2 d12 = make_float2(a[1].x - a[2].x, a[1].y - a[2].y);
-            c[0] = make_float2(a[0].x + s12.x, a[0].y + s12.y);
-            const float2 mid = make_float2(a[0].x - 0.5f * s12.x, a[0].y - 0.5f * s12.y);
-            // -i h d12 = (h d12.y, -h d12.x)
-            c[1] = make_float2(mid.x + h * d12.y, mid.y - h * d12.x);
-            c[2] = make_float2(mid.x - h * d12.y, mid.y + h * d12.x);
-        }
-        y[q + s * (R * p)] = c[0];
-#pragma unroll
-        for (int k = 1; k < R; ++k) y[q + s * (R * p + k)] = cmul(c[k], twiddle(p, k, n));
-    }
-}
-
 __global__ void __launch_bounds__(kPsThreads) flux_ps_kernel(const PsLaunch L)
 {
     extern __shared__ __align__(16) float2 buf[];
     const int N = L.N, H = N / 2 + 1;
     float2* X = buf;
     float2* Y = buf + N;
-    float* acc = reinterpret_cast<float*>(buf + 2 * N);        // H partial powers
+    float2* T = buf + 2 * N;                                   // N twiddles
+    float* acc = reinterpret_cast<float*>(buf + 3 * N);        // H partial powers
     for (int n = threadIdx.x; n < H; n += blockDim.x) acc[n] = 0.f;
+    fft_twiddles(T, N);
     const float inv_mean = (float)((double)L.n_skewers * N / *L.sum);
     const long long pairs = (L.n_skewers + 1) / 2;
     for (long long pr = blockIdx.x; pr < pairs; pr += gridDim.x) {
@@ -249,23 +180,7 @@ __global__ void __launch_bounds__(kPsThreads) flux_ps_kernel(const PsLaunch L)
             X[i] = make_float2(da, db);
         }
         __syncthreads();
-        float2* src = X;
-        float2* dst = Y;
-        int n = N, s = 1;
-        while (n % 3 == 0) {
-            stockham_pass<3>(src, dst, N, n, s);
-            __syncthreads();
-            n /= 3;
-            s *= 3;
-            float2* t = src; src = dst; dst = t;
-        }
-        while (n > 1) {
-            stockham_pass<2>(src, dst, N, n, s);
-            __syncthreads();
-            n /= 2;
-            s *= 2;
-            float2* t = src; src = dst; dst = t;
-        }
+        const float2* src = fft_stockham(X, Y, T, N);
         // Z = A + i B: A_n = (Z_n + conj Z_{N-n}) / 2, B_n = (Z_n - conj Z_{N-n}) / 2i
         for (int k = threadIdx.x; k < H; k += blockDim.x) {
             const float2 z = src[k], zc = src[k == 0 ? 0 : N - k];
@@ -331,7 +246,7 @@ lya_status mock_spectra_run(const float* flux, int64_t n_skewers, int n_pix, int
     return LYA_OK;
 }
 
-size_t flux_ps_smem_bytes(int n_pix) { return sizeof(float2) * 2 * (size_t)n_pix + sizeof(float) * (n_pix / 2 + 1); }
+size_t flux_ps_smem_bytes(int n_pix) { return sizeof(float2) * 3 * (size_t)n_pix + sizeof(float) * (n_pix / 2 + 1); }
 
 lya_status flux_power_run(const float* flux, int64_t n_skewers, int n_pix, double* sums_out /* host: N/2+1 */,
                           double* mean_out, cudaStream_t stream)
