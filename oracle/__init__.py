@@ -59,6 +59,7 @@ class _Params(ctypes.Structure):
         ("omega_b", ctypes.c_double), ("y_he", ctypes.c_double),
         ("t_mode", ctypes.c_int), ("T0", ctypes.c_double), ("gamma", ctypes.c_double),
         ("delta_pivot", ctypes.c_double), ("gamma12", ctypes.c_double),
+        ("profile", ctypes.c_int),
     ]
 
 
@@ -68,6 +69,8 @@ class Params:
 
     ``t_mode`` 0 takes T per pixel from the input array; 1 uses Eq. 5,
     T = T0 (1+delta)^(gamma-1) with T held constant above 1+delta = delta_pivot.
+    ``profile`` 1 averages each line's Gaussian over the pixel's velocity cell
+    instead of sampling it at the pixel's velocity (Eq. 6 as written).
     """
     box: float = 20.0           # h^-1 Mpc
     z: float = 2.5
@@ -81,11 +84,12 @@ class Params:
     gamma: float = 1.5
     delta_pivot: float = 10.0
     gamma12: float = 1.0
+    profile: int = 0            # 0: Eq. 6 sampled at v_H(i); 1: averaged over the pixel cell
 
     def _c(self) -> _Params:
         return _Params(self.box, self.z, self.h, self.omega_m, self.omega_l,
                        self.omega_b, self.y_he, int(self.t_mode), self.T0,
-                       self.gamma, self.delta_pivot, self.gamma12)
+                       self.gamma, self.delta_pivot, self.gamma12, int(self.profile))
 
 
 def _load():

@@ -62,6 +62,9 @@ typedef struct {
     double T0, gamma;    /* Eq. 5                                             */
     double delta_pivot;  /* 1+delta above which T is held constant (10)       */
     double gamma12;      /* photo-ionisation rate in 1e-12 s^-1 (Eq. 4)       */
+    int    profile;      /* 0: Eq. 6 as written, the line profile sampled at the
+                          * pixel velocity; 1: the profile averaged over the
+                          * pixel's velocity cell [v_H - du/2, v_H + du/2)      */
 } orc_params;
 
 /* H(z) in km/s/Mpc for a flat LCDM background (Sec. 2, cosmology). */
@@ -151,8 +154,18 @@ static void tau_one_skewer(const orc_params* p, int64_t N, const float* rho,
             double u_j = (double)j * du + (double)vpec[j];
             double d = nearest_image(vh_i - u_j, V);
             double x = d / b[j];
+            double shape;
+            if (p->profile == 0) {
+                shape = exp(-x * x);
+            } else {
+                /* (1/du) int_{d-du/2}^{d+du/2} exp(-(y/b)^2) dy
+                 *   = (sqrt(pi) b / 2du) [erf((d+du/2)/b) - erf((d-du/2)/b)],
+                 * as a difference of erfc of |d| so the far wings do not cancel */
+                double ax = fabs(x), hw = 0.5 * du / b[j];
+                shape = sqrt(ORC_PI) * b[j] / (2.0 * du) * (erfc(ax - hw) - erfc(ax + hw));
+            }
             /* n_HI/b with b in cm/s, as Eq. 6 is written in cgs */
-            acc += nhi[j] / (b[j] * ORC_KMS_CMS) * exp(-x * x);
+            acc += nhi[j] / (b[j] * ORC_KMS_CMS) * shape;
         }
         tau[i] = pref * acc;
     }

@@ -20,8 +20,8 @@ MUTANTS = [
     ("velocity of the wrong pixel", "double u_j = (double)j * du + (double)vpec[j];",
      "double u_j = (double)j * du + (double)vpec[i];"),
     ("no periodic image", "double d = nearest_image(vh_i - u_j, V);", "double d = vh_i - u_j;"),
-    ("b left in km/s in the prefactor", "acc += nhi[j] / (b[j] * ORC_KMS_CMS) * exp(-x * x);",
-     "acc += nhi[j] / b[j] * exp(-x * x);"),
+    ("b left in km/s in the prefactor", "acc += nhi[j] / (b[j] * ORC_KMS_CMS) * shape;",
+     "acc += nhi[j] / b[j] * shape;"),
     ("Gaussian width off by sqrt 2", "double x = d / b[j];", "double x = d / (b[j] * 1.41421356237);"),
     ("temperature exponent sign", "pow(T / 1.0e4, -0.7)", "pow(T / 1.0e4, 0.7)"),
     ("density to the first power", "* rho * rho * zf * zf * zf;", "* rho * zf * zf * zf;"),
@@ -32,6 +32,11 @@ MUTANTS = [
     ("baryon instead of hydrogen density", "return (1.0 - p->y_he) * p->omega_b", "return p->omega_b"),
     ("Newton step sign", "double An = (gp < 0.0) ? A - g / gp : NAN;", "double An = (gp < 0.0) ? A + g / gp : NAN;"),
     ("PDF bins not centred", "double k = floor((40.0 * F + 1.0) / 2.0);", "double k = floor((40.0 * F) / 2.0);"),
+    ("averaged profile: cell half-width du", "double ax = fabs(x), hw = 0.5 * du / b[j];",
+     "double ax = fabs(x), hw = du / b[j];"),
+    ("averaged profile: b dropped from the cell mean", "shape = sqrt(ORC_PI) * b[j] / (2.0 * du)",
+     "shape = sqrt(ORC_PI) / (2.0 * du)"),
+    ("averaged profile: erfc sum", "(erfc(ax - hw) - erfc(ax + hw))", "(erfc(ax - hw) + erfc(ax + hw))"),
     ("sample variance", "*var = sum_get(&v) / (double)n;\n    *tau_eff = -log(m);\n    return 0;\n}\n\n/* The same",
      "*var = sum_get(&v) / (double)(n - 1);\n    *tau_eff = -log(m);\n    return 0;\n}\n\n/* The same"),
 ]
@@ -49,6 +54,7 @@ def test_pins_catch_mutant(tmp_path, name, old, new):
                    check=True)
     env = dict(os.environ, LYA_ORACLE_LIB=str(so), OMP_NUM_THREADS="2")
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_profile.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"pins did not catch mutant '{name}':\n{r.stdout[-2000:]}"
