@@ -92,7 +92,15 @@ typedef struct {
     double gamma12;      /* H I photo-ionisation rate / 1e-12 s^-1 (> 0)       */
     double nsigma;       /* pairs with |v_H(i)-u(j)| <= nsigma b(j) are summed (8) */
     int precision;       /* LYA_PREC_*                                         */
+    int profile;         /* LYA_PROFILE_SAMPLED: Eq. 6 as written, each line's   */
+                         /* Gaussian sampled at the pixel velocity v_H(i);     */
+                         /* LYA_PROFILE_AVERAGED: the Gaussian averaged over   */
+                         /* the pixel's velocity cell [v_H - du/2, v_H + du/2) */
+                         /* (column density then conserved exactly for any     */
+                         /* b/du; F32 precisions only)                          */
 } lya_extract_params;
+
+enum { LYA_PROFILE_SAMPLED = 0, LYA_PROFILE_AVERAGED = 1 };
 
 typedef struct {
     double mean_flux;    /* <F>                                               */
@@ -381,7 +389,8 @@ lya_status lya_server_autotune(lya_server srv, lya_field field, const lya_extrac
  * extracted with `params` (F32 precisions only), then A solved so that the
  * mean of exp(-A tau) over all its pixels is target_mean_flux.  Returns
  * LYA_EBUDGET if the request alone exceeds the arena, LYA_EINVAL for a bad
- * argument or an id out of range, LYA_ECUDA if the server has failed.
+ * argument or an id out of range (F32 compensated, sampled profile only),
+ * LYA_ECUDA if the server has failed.
  */
 lya_status lya_server_submit(lya_server srv, lya_field field, const lya_extract_params* params,
                              const int64_t* ids, int64_t n_ids, double target_mean_flux,

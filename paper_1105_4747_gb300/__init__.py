@@ -12,6 +12,8 @@ from ._binding import (  # noqa: F401
     PREC_F32_COMPENSATED,
     PREC_F32_NAIVE,
     PREC_F64,
+    PROFILE_AVERAGED,
+    PROFILE_SAMPLED,
     ExtractParams,
     Field,
     FluxStats,

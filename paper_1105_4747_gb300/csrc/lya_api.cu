@@ -144,6 +144,8 @@ lya_status make_tau_launch(lya_field f, const lya_extract_params* p, TauLaunch* 
     if (!(p->gamma12 > 0.0) || !std::isfinite(p->gamma12)) return LYA_EINVAL;
     if (!(p->nsigma >= 1.0 && p->nsigma <= 40.0)) return LYA_EINVAL;
     if (p->precision < LYA_PREC_F32_COMPENSATED || p->precision > LYA_PREC_F64) return LYA_EINVAL;
+    if (p->profile != LYA_PROFILE_SAMPLED && p->profile != LYA_PROFILE_AVERAGED) return LYA_EINVAL;
+    if (p->profile == LYA_PROFILE_AVERAGED && p->precision == LYA_PREC_F64) return LYA_EINVAL;
     const int N = (int)f->desc.n_pix;
     const Physics ph = physics(f->desc, p->gamma12);
     // |v_pec| < c is checked per value; keep |v_pec|/du below 2^29 pixels so the
@@ -164,6 +166,7 @@ lya_status make_tau_launch(lya_field f, const lya_extract_params* p, TauLaunch* 
     }
     const double b_max = ph.b1e4 * std::sqrt(std::fmax(t_max, 0.0) * 1e-4);
     double w = std::floor(p->nsigma * b_max / ph.du + 0.5) + 1.0;
+    if (p->profile == LYA_PROFILE_AVERAGED) w += 1.0;   // the cell average reaches half a pixel further
     if (!(w >= 1.0)) w = 1.0;
     const int w_cap = (N - 1) / 2;
     const int w_max = w > (double)w_cap ? w_cap : (int)w;
@@ -178,6 +181,7 @@ lya_status make_tau_launch(lya_field f, const lya_extract_params* p, TauLaunch* 
     L.err = f->d_err;
     L.w_max = w_max;
     L.t_mode = p->t_mode;
+    L.profile = p->profile;
     L.du_hi = (float)ph.du;
     L.du_lo = (float)(ph.du - (double)L.du_hi);
     L.inv_du = (float)(1.0 / ph.du);

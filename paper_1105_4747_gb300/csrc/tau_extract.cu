@@ -283,6 +283,8 @@ constexpr int kTileKeys = 256;                   // tile-order histogram (counts
 constexpr int kReachLow = -(1 << 28);
 constexpr int kReachHigh = 1 << 28;
 constexpr int kEmptyRun = 30000;                 // L of a tile no source reaches (L > R)
+constexpr float kSqrtLn2 = 0.83255461115769775f;
+constexpr float kHalfSqrtPi = 0.88622692545275801f;
 
 __host__ __device__ __forceinline__ int round_up4(int n) { return (n + 3) & ~3; }
 
@@ -351,22 +353,43 @@ __device__ __forceinline__ void kahan_fold(float& S, float& C, float P)
     S = t;
 }
 
+// The pixel-cell average of exp(-y^2) over [y - hw, y + hw], times 2 hw / sqrt(pi):
+// erf(y + hw) - erf(y - hw), written with erfc of |y| so the far wings do not
+// cancel.
+__device__ __forceinline__ float cell_erf(float y, float hw)
+{
+    const float ay = fabsf(y);
+    return erfcf(ay - hw) - erfcf(ay + hw);
+}
+
 // Two adjacent pixels fo, fo + 1 (in the run's frame) against candidates [k0, k1).
-template <bool COMP>
+// AVG: records hold the averaged-profile constants {du/b, r/b, w sqrt(pi) b/2du, t}.
+template <bool COMP, bool AVG>
 __device__ __forceinline__ void pair2_segment(const float4* __restrict__ rec, int k0, int k1, float fo,
                                               float (&S)[2], float (&C)[2])
 {
+    auto terms = [&](const float4& r, float& t0, float& t1) {
+        const float x0 = fmaf(fo - r.w, r.x, -r.y);                  // r = {a, c r, w, t}
+        const float x1 = x0 + r.x;
+        if constexpr (AVG) {
+            const float hw = 0.5f * r.x;
+            t0 = r.z * cell_erf(x0, hw);
+            t1 = r.z * cell_erf(x1, hw);
+        } else {
+            t0 = r.z * ex2(-(x0 * x0));
+            t1 = r.z * ex2(-(x1 * x1));
+        }
+    };
     int k = k0;
     if constexpr (COMP) {
         while (k < k1) {
             float P0 = 0.f, P1 = 0.f;
             const int kk = min(k + 4, k1);
             for (; k < kk; ++k) {
-                const float4 r = rec[k];                     // {a, c r, w, t}
-                const float x0 = fmaf(fo - r.w, r.x, -r.y);
-                const float x1 = x0 + r.x;
-                P0 = fmaf(r.z, ex2(-(x0 * x0)), P0);
-                P1 = fmaf(r.z, ex2(-(x1 * x1)), P1);
+                float t0, t1;
+                terms(rec[k], t0, t1);
+                P0 += t0;
+                P1 += t1;
             }
             kahan_fold(S[0], C[0], P0);                      // Kahan folds of the block sums
             kahan_fold(S[1], C[1], P1);
@@ -374,11 +397,10 @@ __device__ __forceinline__ void pair2_segment(const float4* __restrict__ rec, in
     } else {
 #pragma unroll 2
         for (; k < k1; ++k) {
-            const float4 r = rec[k];
-            const float x0 = fmaf(fo - r.w, r.x, -r.y);
-            const float x1 = x0 + r.x;
-            S[0] = fmaf(r.z, ex2(-(x0 * x0)), S[0]);
-            S[1] = fmaf(r.z, ex2(-(x1 * x1)), S[1]);
+            float t0, t1;
+            terms(rec[k], t0, t1);
+            S[0] += t0;
+            S[1] += t1;
         }
     }
 }
@@ -388,7 +410,7 @@ __device__ __forceinline__ void pair2_segment(const float4* __restrict__ rec, in
 // holds the group's tile_smem_bytes(N, w_max) bytes (16-byte aligned);
 // warp_tot (33 ints) and tile_hist (kTileKeys ints, 16-byte aligned) are the
 // group's own shared scratch.  N <= MAXQ * g.nt.
-template <bool COMP, int MAXQ>
+template <bool COMP, int MAXQ, bool AVG = false>
 __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __restrict__ rho,
                                             const float* __restrict__ vpec, const float* __restrict__ temp,
                                             float* out, unsigned char* smem, int* warp_tot, int* tile_hist,
@@ -452,7 +474,15 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
         const int j = src_index(q, vec, tid, nt);
         th_[q] = -1;
         if (j < N && r_[q] > 0.f) {
-            const SrcF32 s = prep_f32(L, r_[q], v_[q], T_[q], j);
+            SrcF32 s = prep_f32(L, r_[q], v_[q], T_[q], j);
+            if constexpr (AVG) {
+                // cell average: y = d/b = x sqrt(ln 2), half-width du/2b, weight
+                // w sqrt(pi) b / 2du; the window grows by the half cell
+                s.a *= kSqrtLn2;
+                s.bb *= kSqrtLn2;
+                s.w *= kHalfSqrtPi / s.a;
+                s.h = min(s.h + 1, L.w_max);
+            }
             a_[q] = s.a;
             bb_[q] = s.bb;
             w_[q] = s.w;
@@ -541,7 +571,7 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
         const int o = kTile * tile + 2 * lane_q;
         float S[2] = {0.f, 0.f}, C[2] = {0.f, 0.f};
         for_tile_run(bin, N, Lt[tile], Rt[tile], [&](int k0, int k1, float shift) {
-            pair2_segment<COMP>(rec, k0, k1, (float)o + shift, S, C);
+            pair2_segment<COMP, AVG>(rec, k0, k1, (float)o + shift, S, C);
         });
         if (o < N) tau_s[o] = K * (COMP ? __fsub_rn(S[0], C[0]) : S[0]);
         if (o + 1 < N) tau_s[o + 1] = K * (COMP ? __fsub_rn(S[1], C[1]) : S[1]);
@@ -557,7 +587,7 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
     }
 }
 
-template <bool COMP, int MAXQ>
+template <bool COMP, int MAXQ, bool AVG>
 __global__ void __launch_bounds__(512, MAXQ <= 8 ? 2 : 1) tau_tile_kernel(const TauLaunch L)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -572,7 +602,7 @@ __global__ void __launch_bounds__(512, MAXQ <= 8 ? 2 : 1) tau_tile_kernel(const 
         if (threadIdx.x == 0) atomicOr(L.err, 1);
         return;
     }
-    tile_skewer<COMP, MAXQ>(L, L.rho + sk * (int64_t)N, L.vpec + sk * (int64_t)N,
+    tile_skewer<COMP, MAXQ, AVG>(L, L.rho + sk * (int64_t)N, L.vpec + sk * (int64_t)N,
                             L.temp ? L.temp + sk * (int64_t)N : nullptr, out, smem_raw, warp_tot, tile_hist,
                             whole_block());
 }
@@ -678,15 +708,22 @@ static cudaError_t launch_kernel(K kernel, const TauLaunch& L, size_t smem, cuda
     return cudaGetLastError();
 }
 
-template <bool COMP>
-static cudaError_t launch_tile(const TauLaunch& L, cudaStream_t stream)
+template <bool COMP, bool AVG>
+static cudaError_t launch_tile_profile(const TauLaunch& L, cudaStream_t stream)
 {
     const size_t smem = tile_smem_bytes(L.n_pix, L.w_max);
     const int nt = block_threads(L.n_pix);
     const int q = (L.n_pix + nt - 1) / nt;
-    if (q <= 4) return launch_kernel(tau_tile_kernel<COMP, 4>, L, smem, stream);
-    if (q <= 8) return launch_kernel(tau_tile_kernel<COMP, 8>, L, smem, stream);
-    return launch_kernel(tau_tile_kernel<COMP, 16>, L, smem, stream);
+    if (q <= 4) return launch_kernel(tau_tile_kernel<COMP, 4, AVG>, L, smem, stream);
+    if (q <= 8) return launch_kernel(tau_tile_kernel<COMP, 8, AVG>, L, smem, stream);
+    return launch_kernel(tau_tile_kernel<COMP, 16, AVG>, L, smem, stream);
+}
+
+template <bool COMP>
+static cudaError_t launch_tile(const TauLaunch& L, cudaStream_t stream)
+{
+    return L.profile == LYA_PROFILE_AVERAGED ? launch_tile_profile<COMP, true>(L, stream)
+                                             : launch_tile_profile<COMP, false>(L, stream);
 }
 
 cudaError_t launch_tau(const TauLaunch& L, int precision, cudaStream_t stream)

@@ -395,3 +395,47 @@ def test_fused_stats_equal_separate_call(lya):
     assert st2.var_flux == pytest.approx(st1.var_flux, rel=1e-9)
     A3, F3, st3 = lya.rescale_mean_flux_stats(tau, ls.TINY_20MPC_FT, flux_out=None)
     assert F3 is None and A3 == A1 and np.array_equal(st3.pdf, st1.pdf)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_averaged_profile_tiny_all_skewers(lya, orc, precision):
+    """The pixel-averaged profile against the oracle's, every pixel of the
+    64 x 256 field (b/du ~ 2 there, so the averaging matters at the % level)."""
+    spec = ls.TINY_20MPC
+    rho, v, t = ls.skewers(spec, np.arange(ls.TINY_20MPC_SKEWERS))
+    field = make_field(lya, spec, rho, v, t)
+    tau = lya.extract_skewers(field, lya.ExtractParams(precision=precision, profile=lya.PROFILE_AVERAGED))
+    p = oparams(orc, spec)
+    p.profile = 1
+    tau_o = orc.tau(p, rho, v, t)
+    A_o, _ = orc.rescale(tau_o, ls.TINY_20MPC_FT)
+    assert_tau_close(tau.cpu().numpy(), tau_o, A_o)
+    A, F = lya.rescale_mean_flux(tau.ravel(), ls.TINY_20MPC_FT)
+    assert float(np.abs(F.cpu().numpy() - orc.flux(tau_o.ravel(), A_o)).max()) <= F_ATOL
+    # the sampled and averaged profiles differ here by more than the tolerance
+    tau_s = lya.extract_skewers(field, lya.ExtractParams(precision=precision))
+    assert float((tau_s - tau).abs().max() / tau.abs().max()) > 1e-3
+
+
+def test_averaged_profile_gpc_subset_and_column(lya, orc):
+    """Averaged profile on 16 skewers of the 1 Gpc field (b/du ~ 0.65, where
+    the sampled profile misses absorption between pixels): parity with the
+    oracle, and column density conserved to FP32 rounding."""
+    spec = ls.GPC_4096
+    ids = ls.random_subset(ls.GPC_4096_SKEWERS, 16, 1001)
+    rho, v, t = ls.skewers(spec, ids)
+    field = make_field(lya, spec, rho, v, t)
+    tau = lya.extract_skewers(field, lya.ExtractParams(profile=lya.PROFILE_AVERAGED)).cpu().numpy()
+    p = oparams(orc, spec)
+    p.profile = 1
+    tau_o = orc.tau(p, rho, v, t)
+    A_o, _ = orc.rescale(tau_o, ls.GPC_4096_FT)
+    assert_tau_close(tau, tau_o, A_o)
+    du = orc.pixel_velocity(p, spec.n_pix)
+    dR = orc.pixel_proper_cm(p, spec.n_pix)
+    col = np.array([sum(orc.nhi(p, float(r), float(tt)) for r, tt in zip(rr, ttt) if r > 0)
+                    for rr, ttt in zip(rho, t)])
+    expect = 2.99792458e10 * 4.48e-18 * dR * col / (du * 1e5)
+    assert np.allclose(tau.astype(np.float64).sum(axis=1), expect, rtol=2e-5)
+    with pytest.raises(lya.LyaError):
+        lya.extract_skewers(field, lya.ExtractParams(profile=lya.PROFILE_AVERAGED, precision=lya.PREC_F64))
