@@ -314,6 +314,32 @@ typedef struct {
 lya_status lya_generate_sightlines(const lya_sightline_desc* desc, int64_t n_pix, int64_t first_id,
                                    int64_t n_ids, float* rho_out, float* vpec_out, void* stream);
 
+/*
+ * 3D flux power spectrum of a set of lines of sight, reconstructed with Eq. 7
+ * and spherically averaged.  The lines run
+ * along z through a periodic cube of side box (h^-1 Mpc); line i sits at
+ * transverse cell cells[i] = ix * n_perp + iy (host array) of an n_perp x
+ * n_perp grid.  With delta_F = F / <F> - 1:
+ *   P_box(k)  = (V / M^2) |G_k|^2 of delta_F placed at the lines' cells (0
+ *               elsewhere) on the n_perp^2 x n_pix grid, V = box^3, M cells;
+ *   P_1D(k_z) = (box / n_pix^2) <|D(k_z)|^2> over the lines;
+ *   P_2D,w    = box^2 n_los / n_perp^4, the white level of the lines' weights
+ *               (the 2D weighting power of the line positions away from k_perp = 0);
+ *   P_N       = (box / n_pix) noise_sigma^2 P_2D,w (white noise of rms
+ *               noise_sigma per pixel in delta_F; 0 for noiseless spectra);
+ *   P_true    = P_box - P_1D P_2D,w - P_N                          (Eq. 7),
+ * averaged in shells b <= |k| / k_f < b + 1, k_f = 2 pi / box, b = 0 ..
+ * n_shells - 1 (lya_flux_power_3d_shells), each reporting the mean |k|
+ * (k_mean, h/Mpc), the mean P_true and P_box (h^-3 Mpc^3) and the number of
+ * modes (host arrays of n_shells; k_mean, p_box and n_modes nullable).
+ * flux: device [n_los][n_pix], n_pix = 2^a 3^b; n_perp = 2^a 3^b <= 96.
+ * Transforms in FP32, sums in FP64.  Synchronises the stream.
+ */
+lya_status lya_flux_power_3d_shells(int64_t n_pix, int n_perp, int64_t* n_shells);
+lya_status lya_flux_power_3d(const float* flux, const int32_t* cells, int64_t n_los, int64_t n_pix, int n_perp,
+                             double box, double noise_sigma, double* k_mean, double* p_true, double* p_box,
+                             double* n_modes, void* stream);
+
 /* ======================================================================
  * Serving: a persistent request loop over resident fields.
  *

@@ -24,6 +24,7 @@ from ._binding import (  # noqa: F401
     extract_skewers,
     field_pixel_width,
     flux_power_1d,
+    flux_power_3d,
     generate_sightlines,
     mock_shape,
     mock_spectra,

@@ -129,6 +129,8 @@ def load_library():
         u64 = ctypes.c_uint64
         lib.lya_field_pixel_width.argtypes = [vp, ctypes.POINTER(d)]
         lib.lya_generate_sightlines.argtypes = [ctypes.POINTER(_SightlineDesc), i64, i64, i64, vp, vp, vp]
+        lib.lya_flux_power_3d_shells.argtypes = [i64, i32, ctypes.POINTER(i64)]
+        lib.lya_flux_power_3d.argtypes = [vp, vp, i64, i64, i32, d, d, vp, vp, vp, vp, vp]
         lib.lya_mock_shape.argtypes = [i64, d, ctypes.POINTER(_MockParams), ctypes.POINTER(i64)]
         lib.lya_mock_spectra.argtypes = [vp, i64, i64, d, ctypes.POINTER(_MockParams), vp, vp]
         lib.lya_flux_power_1d.argtypes = [vp, i64, i64, d, vp, vp, ctypes.POINTER(d), vp]
@@ -147,7 +149,8 @@ def load_library():
                      "lya_mean_flux_sums", "lya_flux_at", "lya_server_create", "lya_server_autotune",
                      "lya_server_submit", "lya_server_poll", "lya_server_wait", "lya_server_copy_flux",
                      "lya_server_release", "lya_server_info", "lya_server_destroy", "lya_field_pixel_width",
-                     "lya_mock_shape", "lya_mock_spectra", "lya_flux_power_1d", "lya_generate_sightlines"):
+                     "lya_mock_shape", "lya_mock_spectra", "lya_flux_power_1d", "lya_generate_sightlines",
+                     "lya_flux_power_3d_shells", "lya_flux_power_3d"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -614,3 +617,29 @@ def generate_sightlines(n_pix: int, first_id: int, n_ids: int, *, box: float, z:
                                                   rho_out.data_ptr(), vpec_out.data_ptr(), _stream_handle(stream)),
            "lya_generate_sightlines")
     return rho_out, vpec_out
+
+
+def flux_power_3d(flux, cells, n_perp: int, box: float, noise_sigma: float = 0.0, stream=None):
+    """Shell-averaged Eq. 7 3D flux power of lines of sight (lya_flux_power_3d).
+
+    ``cells``: transverse cell of each line, ix * n_perp + iy (or an [n][2]
+    array of (ix, iy)).  Returns (k_mean, P_true, P_box, n_modes) numpy arrays.
+    """
+    _require_cuda_f32(flux, "flux")
+    if flux.dim() != 2:
+        raise ValueError("flux must be [n_los][n_pix]")
+    S, N = flux.shape
+    c = np.asarray(cells, dtype=np.int64)
+    if c.ndim == 2:
+        c = c[:, 0] * n_perp + c[:, 1]
+    c = np.ascontiguousarray(c.ravel(), dtype=np.int32)
+    if c.size != S:
+        raise ValueError("one cell per line of sight")
+    lib = load_library()
+    ns = ctypes.c_int64()
+    _check(lib.lya_flux_power_3d_shells(N, int(n_perp), ctypes.byref(ns)), "lya_flux_power_3d_shells")
+    k, pt, pb, nm = (np.zeros(ns.value) for _ in range(4))
+    _check(lib.lya_flux_power_3d(flux.data_ptr(), c.ctypes.data, S, N, int(n_perp), float(box), float(noise_sigma),
+                                 k.ctypes.data, pt.ctypes.data, pb.ctypes.data, nm.ctypes.data,
+                                 _stream_handle(stream)), "lya_flux_power_3d")
+    return k, pt, pb, nm

@@ -137,5 +137,67 @@ __device__ inline float2* fft_stockham(float2* X, float2* Y, const float2* T, in
     return src;
 }
 
+
+// Batched, strided form for 2D transforms in shared memory: B transforms of
+// length Nf, transform b's element i at b * bs + i * es (rows: bs = Nf, es = 1;
+// columns: bs = 1, es = Nf).  T holds the Nf twiddles.
+template <int R>
+__device__ __forceinline__ void stockham_pass_batched(const float2* __restrict__ x, float2* __restrict__ y,
+                                                      const float2* __restrict__ T, int Nf, int n, int s, int B,
+                                                      int bs, int es)
+{
+    const int m = n / R, per = Nf / R;
+    const float inv_s = 1.f / (float)s, inv_per = 1.f / (float)per;
+    for (int t = threadIdx.x; t < B * per; t += blockDim.x) {
+        int b, tt, p, q;
+        divmod_small(t, per, inv_per, b, tt);
+        divmod_small(tt, s, inv_s, p, q);
+        const int base = b * bs;
+        float2 a[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) a[j] = x[base + es * (q + s * (p + j * m))];
+        float2 c[R];
+        if constexpr (R == 2) {
+            c[0] = make_float2(a[0].x + a[1].x, a[0].y + a[1].y);
+            c[1] = make_float2(a[0].x - a[1].x, a[0].y - a[1].y);
+        } else {
+            const float h = 0.86602540378443865f;
+            const float2 s12 = make_float2(a[1].x + a[2].x, a[1].y + a[2].y);
+            const float2 d12 = make_float2(a[1].x - a[2].x, a[1].y - a[2].y);
+            c[0] = make_float2(a[0].x + s12.x, a[0].y + s12.y);
+            const float2 mid = make_float2(a[0].x - 0.5f * s12.x, a[0].y - 0.5f * s12.y);
+            c[1] = make_float2(mid.x + h * d12.y, mid.y - h * d12.x);
+            c[2] = make_float2(mid.x - h * d12.y, mid.y + h * d12.x);
+        }
+        y[base + es * (q + s * (R * p))] = c[0];
+#pragma unroll
+        for (int k = 1; k < R; ++k) y[base + es * (q + s * (R * p + k))] = cmul(c[k], T[p * k * s]);
+    }
+}
+
+// B strided transforms of length Nf = 2^a 3^b (B Nf <= 2^16), ping-ponging
+// between X and Y; returns the buffer holding the result.  Ends with a barrier.
+__device__ inline float2* fft_stockham_batched(float2* X, float2* Y, const float2* T, int Nf, int B, int bs, int es)
+{
+    float2* src = X;
+    float2* dst = Y;
+    int n = Nf, s = 1;
+    while (n % 3 == 0) {
+        stockham_pass_batched<3>(src, dst, T, Nf, n, s, B, bs, es);
+        __syncthreads();
+        n /= 3;
+        s *= 3;
+        float2* t = src; src = dst; dst = t;
+    }
+    while (n > 1) {
+        stockham_pass_batched<2>(src, dst, T, Nf, n, s, B, bs, es);
+        __syncthreads();
+        n /= 2;
+        s *= 2;
+        float2* t = src; src = dst; dst = t;
+    }
+    return src;
+}
+
 }  // namespace fftd
 }  // namespace lya

@@ -490,6 +490,44 @@ lya_status lya_generate_sightlines(const lya_sightline_desc* d, int64_t n_pix, i
                                rho_out, vpec_out, static_cast<cudaStream_t>(stream));
 }
 
+lya_status lya_flux_power_3d_shells(int64_t n_pix, int n_perp, int64_t* n_shells)
+{
+    if (!n_shells || n_pix < 2 || n_perp < 2) return LYA_EINVAL;
+    *n_shells = lya::flux3d_shells(n_perp, (int)n_pix);
+    return LYA_OK;
+}
+
+lya_status lya_flux_power_3d(const float* flux, const int32_t* cells, int64_t n_los, int64_t n_pix, int n_perp,
+                             double box, double noise_sigma, double* k_mean, double* p_true, double* p_box,
+                             double* n_modes, void* stream)
+{
+    if (!flux || !cells || !p_true || n_los < 1 || n_los > 0x7fffffffLL) return LYA_EINVAL;
+    if (!two_three_smooth(n_pix) || n_pix > 65536 || !two_three_smooth(n_perp) || n_perp > 96) return LYA_EINVAL;
+    if (!(box > 0.0) || !std::isfinite(box) || !(noise_sigma >= 0.0) || !std::isfinite(noise_sigma)) return LYA_EINVAL;
+    for (int64_t i = 0; i < n_los; ++i)
+        if (cells[i] < 0 || cells[i] >= n_perp * n_perp) return LYA_EINVAL;
+    if (lya::flux3d_los_smem_bytes((int)n_pix) > lya::max_dynamic_smem() ||
+        lya::flux3d_plane_smem_bytes(n_perp, (int)n_pix) > lya::max_dynamic_smem())
+        return LYA_EINVAL;
+    const int ns = lya::flux3d_shells(n_perp, (int)n_pix);
+    double* sh = new (std::nothrow) double[4 * (size_t)ns];
+    if (!sh) return LYA_ENOMEM;
+    const lya_status st = lya::flux_power_3d_run(flux, cells, n_los, (int)n_pix, n_perp, box, noise_sigma, sh, ns,
+                                                 static_cast<cudaStream_t>(stream));
+    if (st == LYA_OK) {
+        const double kf = 2.0 * 3.14159265358979323846 / box;
+        for (int b = 0; b < ns; ++b) {
+            const double c = sh[4 * b + 3];
+            p_true[b] = c > 0.0 ? sh[4 * b] / c : 0.0;
+            if (p_box) p_box[b] = c > 0.0 ? sh[4 * b + 1] / c : 0.0;
+            if (k_mean) k_mean[b] = c > 0.0 ? kf * sh[4 * b + 2] / c : 0.0;
+            if (n_modes) n_modes[b] = c;
+        }
+    }
+    delete[] sh;
+    return st;
+}
+
 lya_status lya_flux_stats(const float* flux, int64_t n, lya_flux_stats_t* out, void* stream)
 {
     if (!flux || n <= 0 || !out) return LYA_EINVAL;

@@ -116,6 +116,15 @@ lya_status sightlines_run(int n_pix, double box, double k_j, double sigma, doubl
                           cudaStream_t stream);
 size_t sightline_smem_bytes(int n_pix);
 
+// 3D flux power of lines of sight on an n_perp^2 transverse grid with the
+// Eq. 7 reconstruction: per shell {sum P_true, sum P_box, sum |m|, modes}.
+lya_status flux_power_3d_run(const float* flux, const int* cells_host, int64_t n_los, int n_pix, int n_perp,
+                             double box, double noise_sigma, double* shells_out, int n_shells,
+                             cudaStream_t stream);
+size_t flux3d_los_smem_bytes(int n_pix);
+size_t flux3d_plane_smem_bytes(int n_perp, int n_pix);
+int flux3d_shells(int n_perp, int n_pix);
+
 // Field validation: counts out-of-domain values and finds the largest T.
 struct FieldCheck {
     unsigned long long bad_rho, bad_vpec, bad_temp;
