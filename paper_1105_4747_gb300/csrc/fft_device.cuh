@@ -147,10 +147,14 @@ __device__ __forceinline__ void stockham_pass_batched(const float2* __restrict__
                                                       int bs, int es)
 {
     const int m = n / R, per = Nf / R;
-    const float inv_s = 1.f / (float)s, inv_per = 1.f / (float)per;
+    const float inv_s = 1.f / (float)s, inv_per = 1.f / (float)per, inv_b = 1.f / (float)B;
     for (int t = threadIdx.x; t < B * per; t += blockDim.x) {
+        // consecutive threads walk the unit-stride direction: along a
+        // transform when es = 1, across transforms when bs = 1 (so a warp's
+        // accesses never stride by a whole row)
         int b, tt, p, q;
-        divmod_small(t, per, inv_per, b, tt);
+        if (es == 1) divmod_small(t, per, inv_per, b, tt);
+        else divmod_small(t, B, inv_b, tt, b);
         divmod_small(tt, s, inv_s, p, q);
         const int base = b * bs;
         float2 a[R];

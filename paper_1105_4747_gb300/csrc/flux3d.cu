@@ -10,7 +10,10 @@
 // shared memory (batched rows, then batched columns) and folds every mode's
 // |G|^2, less the Eq. 7 terms P_1D(k_z) P_2D,w and P_N, into the spherical
 // shells [b, b + 1) k_f that plane can reach (an exact integer square root
-// picks the shell), in shared memory, then once per shell into FP64 totals.
+// picks the shell).  The modes are visited in order of mx^2 + my^2, so a
+// thread's run of modes stays in one or two shells and adds to the shared
+// sums only when its shell changes; the shared sums go once per shell into
+// the FP64 totals.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -106,13 +109,13 @@ __global__ void __launch_bounds__(kLosThreads) f3_los_kernel(const LosLaunch L)
 
 struct PlaneLaunch {
     const float2* planes;
+    const short* order;       // the n^2 transverse modes sorted by mx^2 + my^2
     int n, N;                 // transverse side, pixels per line
     const double* p1d;        // sums of |D|^2 over lines
     double box_norm;          // V / M^2
     double alias;             // (L / N^2) / n_los * P_2D,w: multiplies p1d sums
     double noise;             // P_N
-    double kf;                // fundamental frequency
-    double* shells;           // [n_shells][4]: sum P_true, sum P_box, sum |k|, modes
+    double* shells;           // [n_shells][4]: sum P_true, sum P_box, sum |m|, modes
     int n_shells;
 };
 
@@ -122,6 +125,32 @@ __device__ __forceinline__ int isqrt_exact(int m2)
     while ((b + 1) * (b + 1) <= m2) ++b;
     while (b * b > m2) --b;
     return b;
+}
+
+// fftfreq order: index i of n -> signed mode number
+__device__ __forceinline__ int mode_number(int i, int n) { return i <= (n - 1) / 2 ? i : i - n; }
+
+// The n^2 transverse modes sorted by mx^2 + my^2 (a counting sort in one CTA):
+// for any k_z the shell index is non-decreasing along this order.
+__global__ void __launch_bounds__(kPlaneThreads) f3_order_kernel(int n, short* order)
+{
+    extern __shared__ int keys[];                      // 2 (n/2)^2 + 2 counters
+    const int K = 2 * (n / 2) * (n / 2) + 1;
+    __shared__ int warp_tot[33];
+    for (int k = threadIdx.x; k < K; k += blockDim.x) keys[k] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+        const int mx = mode_number(i / n, n), my = mode_number(i % n, n);
+        atomicAdd(&keys[mx * mx + my * my], 1);
+    }
+    __syncthreads();
+    block_exclusive_scan(keys, K, warp_tot);
+    // stable within a key by mode index: one thread places every mode
+    if (threadIdx.x == 0)
+        for (int i = 0; i < n * n; ++i) {
+            const int mx = mode_number(i / n, n), my = mode_number(i % n, n);
+            order[keys[mx * mx + my * my]++] = (short)i;
+        }
 }
 
 // One k_z plane: 2D transform, Eq. 7, shells.
@@ -147,19 +176,40 @@ __global__ void __launch_bounds__(kPlaneThreads) f3_plane_kernel(const PlaneLaun
     float2* G = fft_stockham_batched(R, O, T, n, n, 1, n);              // columns
     const float mult = (kz == 0 || 2 * kz == P.N) ? 1.f : 2.f;
     const double sub = P.alias * P.p1d[kz] + P.noise;
-    for (int i = threadIdx.x; i < cells; i += blockDim.x) {
-        const int ix = i / n, iy = i - ix * n;
-        const int mx = ix <= n / 2 - (n % 2 == 0 ? 1 : 0) ? ix : ix - n;   // numpy fftfreq order
-        const int my = iy <= n / 2 - (n % 2 == 0 ? 1 : 0) ? iy : iy - n;
+    // each thread takes a contiguous run of the sorted modes, where the shell
+    // changes rarely, and adds to the shared sums only when it does
+    const int per = (cells + blockDim.x - 1) / blockDim.x;
+    const int lo = threadIdx.x * per, hi = min(cells, lo + per);
+    int cur = -1;
+    float s_t = 0.f, s_b = 0.f, s_k = 0.f, s_n = 0.f;
+    for (int j = lo; j < hi; ++j) {
+        const int i = P.order[j];
+        const int mx = mode_number(i / n, n), my = mode_number(i % n, n);
         const int m2 = mx * mx + my * my + kz * kz;
         if (m2 == 0) continue;
         const int b = isqrt_exact(m2) - b0;
+        if (b != cur) {
+            if (cur >= 0) {
+                atomicAdd(&sacc[4 * cur], s_t);
+                atomicAdd(&sacc[4 * cur + 1], s_b);
+                atomicAdd(&sacc[4 * cur + 2], s_k);
+                atomicAdd(&sacc[4 * cur + 3], s_n);
+            }
+            cur = b;
+            s_t = s_b = s_k = s_n = 0.f;
+        }
         const float2 g = G[i];
         const double pbox = P.box_norm * ((double)g.x * g.x + (double)g.y * g.y);
-        atomicAdd(&sacc[4 * b], mult * (float)(pbox - sub));
-        atomicAdd(&sacc[4 * b + 1], mult * (float)pbox);
-        atomicAdd(&sacc[4 * b + 2], mult * sqrtf((float)m2));
-        atomicAdd(&sacc[4 * b + 3], mult);
+        s_t += mult * (float)(pbox - sub);
+        s_b += mult * (float)pbox;
+        s_k += mult * sqrtf((float)m2);
+        s_n += mult;
+    }
+    if (cur >= 0) {
+        atomicAdd(&sacc[4 * cur], s_t);
+        atomicAdd(&sacc[4 * cur + 1], s_b);
+        atomicAdd(&sacc[4 * cur + 2], s_k);
+        atomicAdd(&sacc[4 * cur + 3], s_n);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < 4 * nb; i += blockDim.x) {
@@ -228,16 +278,23 @@ lya_status flux_power_3d_run(const float* flux, const int* cells_host, int64_t n
             e = cudaGetLastError();
         }
     }
+    short* order = nullptr;
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&order, sizeof(short) * (size_t)cells, stream);
+    if (e == cudaSuccess) {
+        const size_t smem_keys = sizeof(int) * (2 * (size_t)(n_perp / 2) * (n_perp / 2) + 2);
+        f3_order_kernel<<<1, kPlaneThreads, smem_keys, stream>>>(n_perp, order);
+        count_launch();
+        e = cudaGetLastError();
+    }
     const size_t smem_plane = flux3d_plane_smem_bytes(n_perp, n_pix);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(f3_plane_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_plane);
     if (e == cudaSuccess) {
         const double M = (double)cells * n_pix;
         const double p2d = box * box * (double)n_los / ((double)cells * cells);     // white level of the weights
-        PlaneLaunch P{planes, n_perp, n_pix, d + 1, box * box * box / (M * M),
+        PlaneLaunch P{planes, order, n_perp, n_pix, d + 1, box * box * box / (M * M),
                       box / ((double)n_pix * n_pix) / (double)n_los * p2d,
-                      box / n_pix * noise_sigma * noise_sigma * p2d, 2.0 * 3.14159265358979323846 / box,
-                      d + 1 + H, n_shells};
+                      box / n_pix * noise_sigma * noise_sigma * p2d, d + 1 + H, n_shells};
         f3_plane_kernel<<<H, kPlaneThreads, smem_plane, stream>>>(P);
         count_launch();
         e = cudaGetLastError();
@@ -248,6 +305,7 @@ lya_status flux_power_3d_run(const float* flux, const int* cells_host, int64_t n
     if (ticket) cudaFreeAsync(ticket, stream);
     if (cell) cudaFreeAsync(cell, stream);
     if (planes) cudaFreeAsync(planes, stream);
+    if (order) cudaFreeAsync(order, stream);
     const cudaError_t e2 = cudaStreamSynchronize(stream);
     if (e == cudaSuccess) e = e2;
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LYA_ENOMEM : LYA_ECUDA;
