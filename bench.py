@@ -41,12 +41,12 @@ UNIT = "pixels/s"
 WORKLOAD = "gpc_box_65536x4096_z2.5"
 ALG_BYTES_PER_PX = 16          # rho, vpec, T read (12 B) + tau written (4 B)
 # DRAM bytes of one tau-kernel launch per skewer, from the ncu captures in
-# profiles/ (8,192 skewers of the Gpc workload; 262,144 rows of the grid),
+# profiles/ (8,192 skewers of the Gpc workload; 131,072 rows of the grid),
 # scaled by the number of skewers, with the SHA-1 of the kernel source each
 # was taken on: reported as null once paper_1105_4747_gb300/csrc/tau_extract.cu
 # differs from it.
-TAU_DRAM_PROFILE = {"gpc": ((402.720512e6 + 76.045056e6) / 8192, "0476ec601baaed7a36ecedebcd4a657d3c15381e"),
-                    "grid1536": ((4.832250e9 + 1.551512e9) / 262144, "baa23b9688d05ea3c8c3be43ac9154216f7b199f")}
+TAU_DRAM_PROFILE = {"gpc": ((402.719744e6 + 75.848960e6) / 8192, "98c28325945f533e27dd4f697c35075f0fca4c56"),
+                    "grid1536": ((2.416009e9 + 0.744351e9) / 131072, "98c28325945f533e27dd4f697c35075f0fca4c56")}
 
 
 def workload_config(spec, S, extra=None, grid=False):
