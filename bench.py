@@ -393,6 +393,30 @@ def run_post(lya, torch, field, F, S, spec, reps):
     ev[1].synchronize()
     ms_avg = ev[0].elapsed_time(ev[1]) / reps
     del tau_avg
+    # an oversampled field (b/du ~ 26: 8,192-pixel lines of sight through a
+    # 50 h^-1 Mpc box, the short end of the served boxes), generated on the
+    # device, extracted with each way of forming the pair sum's exponentials
+    o_n, o_S, o_box = 8192, 4096, 50.0
+    o_rho = torch.empty((o_S, o_n), dtype=torch.float32, device="cuda")
+    o_v = torch.empty_like(o_rho)
+    lya.generate_sightlines(o_n, 0, o_S, rho_out=o_rho, vpec_out=o_v, box=o_box, z=spec.z, k_j=spec.k_j,
+                            sigma_delta=spec.sigma_delta, seed=spec.seed + 1)
+    o_field = lya.Field(o_rho, o_v, None, box=o_box, z=spec.z, borrow=True)
+    o_tau = torch.empty_like(o_rho)
+    o_ms = {}
+    for name, em in (("mufu", lya.EXP_MUFU), ("recurrence", lya.EXP_RECURRENCE),
+                     ("poly_split", lya.EXP_POLY_SPLIT)):
+        p_o = lya.ExtractParams(t_mode=1, T0=1.5e4, gamma=1.5, exp_method=em)
+        lya.extract_skewers(o_field, p_o, out=o_tau)
+        ev[0].record(stream)
+        for _ in range(reps):
+            lya.extract_skewers(o_field, p_o, out=o_tau)
+        ev[1].record(stream)
+        ev[1].synchronize()
+        o_ms[name] = ev[0].elapsed_time(ev[1]) / reps
+    o_du = lya.field_pixel_width(o_field)
+    o_field.close()
+    del o_rho, o_v, o_tau
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     n_px = S * spec.n_pix
@@ -404,6 +428,12 @@ def run_post(lya, torch, field, F, S, spec, reps):
                              "roofline": {"bound": "hbm", "achieved": b_mock / (ms_mock / 1e3) / 1e9, "peak": peak,
                                           "unit": "GB/s", "frac": b_mock / (ms_mock / 1e3) / 1e9 / peak,
                                           "alg_bytes_per_launch": b_mock}},
+            "tau_oversampled": {"workload": f"{o_S} lines x {o_n} px, {o_box:g} h^-1 Mpc box (du {o_du:.3f} km/s, "
+                                            "T = 1.5e4 K Delta^0.5), generated on the device",
+                                "ms": o_ms, "px_per_s": {k: o_S * o_n / (v / 1e3) for k, v in o_ms.items()},
+                                "note": "tau_tile_kernel, 1,024-thread CTAs, four-pixel lanes; exp_method mufu "
+                                        "(one MUFU ex2 per pair), recurrence (Gaussian recurrence, three MUFU per "
+                                        "four pairs), poly_split (one exp2 in four on the FMA pipe)"},
             "tau_averaged_profile": {"ms": ms_avg, "px_per_s": n_px / (ms_avg / 1e3),
                                      "roofline": {"bound": "hbm", "achieved": 16 * n_px / (ms_avg / 1e3) / 1e9,
                                                   "peak": peak, "unit": "GB/s",

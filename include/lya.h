@@ -98,9 +98,21 @@ typedef struct {
                          /* the pixel's velocity cell [v_H - du/2, v_H + du/2) */
                          /* (column density then conserved exactly for any     */
                          /* b/du; F32 precisions only)                          */
+    int exp_method;      /* how the pair sum's exponentials exp(-(d/b)^2) of   */
+                         /* Eq. 6 are evaluated (F32 precisions, sampled        */
+                         /* profile; extraction only, not the serving loop):   */
+                         /* LYA_EXP_MUFU: one MUFU ex2 per pair (default);     */
+                         /* LYA_EXP_RECURRENCE: a lane takes four pixels of a  */
+                         /* line from three exponentials by the Gaussian       */
+                         /* recurrence (Greengard & Lee 2004), lines with      */
+                         /* b >= 2.4 du; LYA_EXP_POLY_SPLIT: one in four       */
+                         /* exponentials by an FMA-pipe polynomial.  All three */
+                         /* meet the same tolerance; they differ in which      */
+                         /* pipe does the work                                 */
 } lya_extract_params;
 
 enum { LYA_PROFILE_SAMPLED = 0, LYA_PROFILE_AVERAGED = 1 };
+enum { LYA_EXP_MUFU = 0, LYA_EXP_RECURRENCE = 1, LYA_EXP_POLY_SPLIT = 2 };
 
 typedef struct {
     double mean_flux;    /* <F>                                               */
@@ -415,8 +427,8 @@ lya_status lya_server_autotune(lya_server srv, lya_field field, const lya_extrac
  * extracted with `params` (F32 precisions only), then A solved so that the
  * mean of exp(-A tau) over all its pixels is target_mean_flux.  Returns
  * LYA_EBUDGET if the request alone exceeds the arena, LYA_EINVAL for a bad
- * argument or an id out of range (F32 compensated, sampled profile only),
- * LYA_ECUDA if the server has failed.
+ * argument or an id out of range (F32 compensated, sampled profile, MUFU
+ * exponentials only), LYA_ECUDA if the server has failed.
  */
 lya_status lya_server_submit(lya_server srv, lya_field field, const lya_extract_params* params,
                              const int64_t* ids, int64_t n_ids, double target_mean_flux,

@@ -12,6 +12,9 @@ from ._binding import (  # noqa: F401
     PREC_F32_COMPENSATED,
     PREC_F32_NAIVE,
     PREC_F64,
+    EXP_MUFU,
+    EXP_POLY_SPLIT,
+    EXP_RECURRENCE,
     PROFILE_AVERAGED,
     PROFILE_SAMPLED,
     ExtractParams,

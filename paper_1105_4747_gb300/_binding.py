@@ -25,6 +25,7 @@ LYA_OK, LYA_EINVAL, LYA_ENOMEM, LYA_ECUDA, LYA_ENOCONV, LYA_ETIMEDOUT, LYA_EBUDG
 SRC_HOST, SRC_DEVICE_COPY, SRC_DEVICE_BORROW = 0, 1, 2
 PREC_F32_COMPENSATED, PREC_F32_NAIVE, PREC_F64 = 0, 1, 2
 PROFILE_SAMPLED, PROFILE_AVERAGED = 0, 1
+EXP_MUFU, EXP_RECURRENCE, EXP_POLY_SPLIT = 0, 1, 2
 
 
 class LyaError(RuntimeError):
@@ -47,7 +48,8 @@ class _FieldDesc(ctypes.Structure):
 class _ExtractParams(ctypes.Structure):
     _fields_ = [("t_mode", ctypes.c_int), ("T0", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("delta_pivot", ctypes.c_double), ("gamma12", ctypes.c_double),
-                ("nsigma", ctypes.c_double), ("precision", ctypes.c_int), ("profile", ctypes.c_int)]
+                ("nsigma", ctypes.c_double), ("precision", ctypes.c_int), ("profile", ctypes.c_int),
+                ("exp_method", ctypes.c_int)]
 
 
 class _FluxStats(ctypes.Structure):
@@ -192,11 +194,12 @@ class ExtractParams:
     nsigma: float = 8.0
     precision: int = PREC_F32_COMPENSATED
     profile: int = 0                    # PROFILE_SAMPLED (Eq. 6) or PROFILE_AVERAGED
+    exp_method: int = 0                 # EXP_MUFU, EXP_RECURRENCE or EXP_POLY_SPLIT
 
     def _c(self) -> _ExtractParams:
         return _ExtractParams(int(self.t_mode), float(self.T0), float(self.gamma),
                               float(self.delta_pivot), float(self.gamma12), float(self.nsigma),
-                              int(self.precision), int(self.profile))
+                              int(self.precision), int(self.profile), int(self.exp_method))
 
 
 class Field:

@@ -146,6 +146,9 @@ lya_status make_tau_launch(lya_field f, const lya_extract_params* p, TauLaunch* 
     if (p->precision < LYA_PREC_F32_COMPENSATED || p->precision > LYA_PREC_F64) return LYA_EINVAL;
     if (p->profile != LYA_PROFILE_SAMPLED && p->profile != LYA_PROFILE_AVERAGED) return LYA_EINVAL;
     if (p->profile == LYA_PROFILE_AVERAGED && p->precision == LYA_PREC_F64) return LYA_EINVAL;
+    if (p->exp_method < LYA_EXP_MUFU || p->exp_method > LYA_EXP_POLY_SPLIT) return LYA_EINVAL;
+    if (p->exp_method != LYA_EXP_MUFU && (p->precision == LYA_PREC_F64 || p->profile != LYA_PROFILE_SAMPLED))
+        return LYA_EINVAL;
     const int N = (int)f->desc.n_pix;
     const Physics ph = physics(f->desc, p->gamma12);
     // |v_pec| < c is checked per value; keep |v_pec|/du below 2^29 pixels so the
@@ -182,6 +185,7 @@ lya_status make_tau_launch(lya_field f, const lya_extract_params* p, TauLaunch* 
     L.w_max = w_max;
     L.t_mode = p->t_mode;
     L.profile = p->profile;
+    L.exp_method = p->exp_method;
     L.du_hi = (float)ph.du;
     L.du_lo = (float)(ph.du - (double)L.du_hi);
     L.inv_du = (float)(1.0 / ph.du);

@@ -46,6 +46,7 @@ struct TauLaunch {
 
     int t_mode;               // 0 stored T, 1 power law (Eq. 5)
     int profile;              // LYA_PROFILE_SAMPLED (Eq. 6) or LYA_PROFILE_AVERAGED
+    int exp_method;           // LYA_EXP_*
     // FP32 forms
     float du_hi, du_lo;       // pixel velocity width as a double-float (km/s)
     float inv_du;             // 1/du

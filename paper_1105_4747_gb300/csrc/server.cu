@@ -418,7 +418,8 @@ lya_status lya_server_submit(lya_server s, lya_field f, const lya_extract_params
 {
     if (!s || !f || !p || !ids || n_ids < 1 || !ticket) return LYA_EINVAL;
     if (!(target > 0.0 && target < 1.0)) return LYA_EINVAL;
-    if (p->precision != LYA_PREC_F32_COMPENSATED || p->profile != LYA_PROFILE_SAMPLED) return LYA_EINVAL;
+    if (p->precision != LYA_PREC_F32_COMPENSATED || p->profile != LYA_PROFILE_SAMPLED ||
+        p->exp_method != LYA_EXP_MUFU) return LYA_EINVAL;
     if (f->device != s->device) return LYA_EINVAL;
     if (n_ids > 0x7fffffffLL / f->desc.n_pix) return LYA_EINVAL;
     ReqHost r;
@@ -530,7 +531,8 @@ lya_status lya_server_autotune(lya_server s, lya_field f, const lya_extract_para
                                int* shift_out)
 {
     if (!s || !f || !p || max_rows < 1) return LYA_EINVAL;
-    if (p->precision != LYA_PREC_F32_COMPENSATED || p->profile != LYA_PROFILE_SAMPLED || f->device != s->device)
+    if (p->precision != LYA_PREC_F32_COMPENSATED || p->profile != LYA_PROFILE_SAMPLED ||
+        p->exp_method != LYA_EXP_MUFU || f->device != s->device)
         return LYA_EINVAL;
     TauLaunch L;
     lya_status st = lya::make_tau_launch(f, p, &L);

@@ -22,6 +22,7 @@
 //   w_j = rho_j^2 (T_j/1e4)^-1.2          (n_HI / b of Eq. 4 and Eq. 6 up to K)
 //   c_j = sqrt(log2 e) / b_j,  a_j = c_j du,   so exp(-(d/b)^2) = 2^-(c d)^2.
 // Per pair: x = fma(m, a_j, -c_j r_j); tau += w_j * ex2(-x*x).
+#include <algorithm>
 #include <cfloat>
 #include <cstdint>
 
@@ -299,6 +300,8 @@ __host__ __device__ inline size_t tile_smem_bytes(int n_pix, int w_max)
 // One warp group of the serving kernel: its tile arrays, then 36 ints of scan
 // scratch and the tile-order histogram.
 constexpr int kGroupScanInts = 36;
+constexpr int kRunTotal = 34;                    // scan scratch slot: the skewer's summed tile runs
+constexpr int kLongRun = 256;                    // mean run per tile from which a lane takes four pixels
 __host__ __device__ inline size_t group_smem_bytes(int n_pix, int w_max)
 {
     return (tile_smem_bytes(n_pix, w_max) + 15) / 16 * 16 + sizeof(int) * (kGroupScanInts + kTileKeys);
@@ -405,12 +408,132 @@ __device__ __forceinline__ void pair2_segment(const float4* __restrict__ rec, in
     }
 }
 
+// 2^y for y <= 0 on the FMA pipe: Cody-Waite split y = n + f (n the nearest
+// integer, by the 1.5 * 2^23 shifter; |f| <= 1/2), 2^f by a degree-5
+// polynomial fitted by least squares on Chebyshev nodes of [-1/2, 1/2]
+// (coefficients from exp2_poly_fit.py beside this file), 2^n written into the
+// exponent field.  Relative error ~2.3e-7; y is clamped at -126, so terms far
+// outside a line's window come out as 2^-126 of its weight instead of 0.
+__device__ __forceinline__ float exp2_poly(float y)
+{
+    y = fmaxf(y, -126.f);
+    const float shifter = 0x1.8p23f;
+    const float t = y + shifter;
+    const int n = __float_as_int(t) - __float_as_int(shifter);
+    const float f = y - (t - shifter);
+    float p = 0x1.5f48c8p-10f;
+    p = fmaf(p, f, 0x1.3d107cp-7f);
+    p = fmaf(p, f, 0x1.c6aeccp-5f);
+    p = fmaf(p, f, 0x1.ebf906p-3f);
+    p = fmaf(p, f, 0x1.62e43p-1f);
+    p = fmaf(p, f, 0x1.000002p+0f);
+    return p * __int_as_float((n << 23) + 0x3f800000);
+}
+
+// Largest a = du sqrt(log2 e)/b for which the Gaussian recurrence is used: three
+// steps then move x by at most 1.5, so a chain that starts below 2^-126 (|x| >
+// 11.2) cannot reach a term above 2^-94 of the line's peak, below the window's
+// own cut.
+constexpr float kRecMaxA = 0.5f;
+
+// Four adjacent pixels fo .. fo + 3 against candidates [k0, k1) (long runs:
+// a record read from shared memory serves four pixels).  EXP selects how the
+// four exponentials 2^-x_m^2, x_m = x_0 + m a, are formed:
+//   LYA_EXP_MUFU        four MUFU ex2;
+//   LYA_EXP_RECURRENCE  the Gaussian recurrence of fast Gaussian gridding
+//                       (Greengard & Lee 2004): E_{m+1} = E_m Q_m,
+//                       Q_{m+1} = Q_m R with Q_0 = 2^-a(2 x_0 + a), R = 2^-2a^2:
+//                       three MUFU and two FMUL per further pixel (lines with
+//                       a <= kRecMaxA; wider pixels take the MUFU form);
+//   LYA_EXP_POLY_SPLIT  three MUFU and one exp2_poly on the FMA pipe.
+template <bool COMP, bool AVG, int EXP>
+__device__ __forceinline__ void pair4_segment(const float4* __restrict__ rec, int k0, int k1, float fo,
+                                              float (&S)[4], float (&C)[4])
+{
+    auto terms = [&](const float4& r, float (&t)[4]) {
+        const float x0 = fmaf(fo - r.w, r.x, -r.y);                  // r = {a, c r, w, t}
+        if constexpr (AVG) {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) t[m] = r.z * cell_erf(fmaf((float)m, r.x, x0), 0.5f * r.x);
+        } else if constexpr (EXP == LYA_EXP_RECURRENCE) {
+            if (r.x <= kRecMaxA) {
+                float E = ex2(-(x0 * x0));
+                float Q = ex2(fminf(-r.x * fmaf(2.f, x0, r.x), 126.f));
+                const float R = ex2(-2.f * r.x * r.x);
+                t[0] = r.z * E;
+#pragma unroll
+                for (int m = 1; m < 4; ++m) {
+                    E *= Q;
+                    Q *= R;
+                    t[m] = r.z * E;
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const float x = fmaf((float)m, r.x, x0);
+                    t[m] = r.z * ex2(-(x * x));
+                }
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const float x = fmaf((float)m, r.x, x0);
+                t[m] = r.z * ((EXP == LYA_EXP_POLY_SPLIT && m == 3) ? exp2_poly(-(x * x)) : ex2(-(x * x)));
+            }
+        }
+    };
+    int k = k0;
+    if constexpr (COMP) {
+        while (k < k1) {
+            float P[4] = {0.f, 0.f, 0.f, 0.f};
+            const int kk = min(k + 4, k1);
+            for (; k < kk; ++k) {
+                float t[4];
+                terms(rec[k], t);
+#pragma unroll
+                for (int m = 0; m < 4; ++m) P[m] += t[m];
+            }
+#pragma unroll
+            for (int m = 0; m < 4; ++m) kahan_fold(S[m], C[m], P[m]);
+        }
+    } else {
+        for (; k < k1; ++k) {
+            float t[4];
+            terms(rec[k], t);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) S[m] += t[m];
+        }
+    }
+}
+
+// Step 7 with two lanes per tile, four pixels each, over the tiles in order.
+template <bool COMP, bool AVG, int EXP>
+__device__ __forceinline__ void tiles_by_four(const float4* __restrict__ rec, const int* bin, const short* Lt,
+                                              const short* Rt, const short* order, int N, int NT, float K,
+                                              float* tau_s, int tid, int nt)
+{
+    const int half = tid & 1, ng = nt / 2, grp = tid / 2;
+    for (int round = 0; round * ng < NT; ++round) {
+        const int i = round * ng + ((round & 1) ? ng - 1 - grp : grp);
+        if (i >= NT) continue;
+        const int tile = order[i];
+        const int o = kTile * tile + 4 * half;
+        float S[4] = {0.f, 0.f, 0.f, 0.f}, C[4] = {0.f, 0.f, 0.f, 0.f};
+        for_tile_run(bin, N, Lt[tile], Rt[tile], [&](int k0, int k1, float shift) {
+            pair4_segment<COMP, AVG, EXP>(rec, k0, k1, (float)o + shift, S, C);
+        });
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+            if (o + m < N) tau_s[o + m] = K * (COMP ? __fsub_rn(S[m], C[m]) : S[m]);
+    }
+}
+
 // One skewer by one group of threads (the whole block, or a run of warps of
 // it): rho/vpec/temp are the skewer's input rows, out its tau row.  smem
 // holds the group's tile_smem_bytes(N, w_max) bytes (16-byte aligned);
-// warp_tot (33 ints) and tile_hist (kTileKeys ints, 16-byte aligned) are the
+// warp_tot (kGroupScanInts ints) and tile_hist (kTileKeys ints, 16-byte aligned) are the
 // group's own shared scratch.  N <= MAXQ * g.nt.
-template <bool COMP, int MAXQ, bool AVG = false>
+template <bool COMP, int MAXQ, bool AVG = false, bool ALT_EXP = false>
 __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __restrict__ rho,
                                             const float* __restrict__ vpec, const float* __restrict__ temp,
                                             float* out, unsigned char* smem, int* warp_tot, int* tile_hist,
@@ -463,6 +586,7 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
     for (int k = tid - 4; k < N; k += nt) cnt[k] = 0;
     for (int e = tid; e < NE; e += nt) reach[e] = kReachLow;
     for (int k = tid; k < kTileKeys; k += nt) tile_hist[k] = 0;
+    if (tid == 0) warp_tot[kRunTotal] = 0;
     g.sync();
 
     // 2. per-source constants (kept in registers) and the histogram of target
@@ -540,6 +664,7 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
     // 6. tiles ordered by candidate count, largest first (counting sort)
     constexpr int kMaxTilesPerThread = (MAXQ + kTile - 1) / kTile;   // NT <= MAXQ nt / kTile
     int tkey[kMaxTilesPerThread];
+    int runs = 0;
 #pragma unroll
     for (int u = 0; u < kMaxTilesPerThread; ++u) {
         const int tile = tid + u * nt;
@@ -549,8 +674,10 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
             for_tile_run(bin, N, Lt[tile], Rt[tile], [&](int k0, int k1, float) { c += k1 - k0; });
             tkey[u] = kTileKeys - 1 - min(c, kTileKeys - 1);
             atomicAdd(&tile_hist[tkey[u]], 1);
+            runs += c;
         }
     }
+    if (runs) atomicAdd(&warp_tot[kRunTotal], runs);
     g.sync();
     block_exclusive_scan(tile_hist, kTileKeys, warp_tot, g);
 #pragma unroll
@@ -560,9 +687,22 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
 
     // 7. lane groups walk the tiles in that order (reversed on alternate
     //    rounds, so every warp's total work evens out); each lane owns two
-    //    adjacent pixels; tau goes to shared memory (the reach array is free)
-    const int lane_q = tid & (kLanesPerTile - 1);
+    //    adjacent pixels, or four where the runs are long; tau goes to shared
+    //    memory (the reach array is free)
     const float K = L.K;
+    if (ALT_EXP && L.exp_method != LYA_EXP_MUFU) {
+        if constexpr (ALT_EXP && !AVG) {
+            if (L.exp_method == LYA_EXP_RECURRENCE)
+                tiles_by_four<COMP, false, LYA_EXP_RECURRENCE>(rec, bin, Lt, Rt, order, N, NT, K, tau_s, tid, nt);
+            else
+                tiles_by_four<COMP, false, LYA_EXP_POLY_SPLIT>(rec, bin, Lt, Rt, order, N, NT, K, tau_s, tid, nt);
+        }
+        g.sync();
+    } else if (warp_tot[kRunTotal] >= kLongRun * NT) {
+        tiles_by_four<COMP, AVG, LYA_EXP_MUFU>(rec, bin, Lt, Rt, order, N, NT, K, tau_s, tid, nt);
+        g.sync();
+    } else {
+    const int lane_q = tid & (kLanesPerTile - 1);
     const int npairs = nt / kLanesPerTile, pair = tid / kLanesPerTile;
     for (int round = 0; round * npairs < NT; ++round) {
         const int i = round * npairs + ((round & 1) ? npairs - 1 - pair : pair);
@@ -577,6 +717,7 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
         if (o + 1 < N) tau_s[o + 1] = K * (COMP ? __fsub_rn(S[1], C[1]) : S[1]);
     }
     g.sync();
+    }
 
     // 8. tau to HBM in order
     if (vec && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
@@ -587,11 +728,11 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
     }
 }
 
-template <bool COMP, int MAXQ, bool AVG>
-__global__ void __launch_bounds__(512, MAXQ <= 8 ? 2 : 1) tau_tile_kernel(const TauLaunch L)
+template <bool COMP, int MAXQ, bool AVG, int NTB>
+__global__ void __launch_bounds__(NTB, NTB >= 1024 ? 1 : 2) tau_tile_kernel(const TauLaunch L)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int warp_tot[33];
+    __shared__ int warp_tot[kGroupScanInts];
     __shared__ __align__(16) int tile_hist[kTileKeys];
     const int64_t row = blockIdx.x;
     const int64_t sk = L.ids ? L.ids[row] : row;
@@ -602,7 +743,7 @@ __global__ void __launch_bounds__(512, MAXQ <= 8 ? 2 : 1) tau_tile_kernel(const 
         if (threadIdx.x == 0) atomicOr(L.err, 1);
         return;
     }
-    tile_skewer<COMP, MAXQ, AVG>(L, L.rho + sk * (int64_t)N, L.vpec + sk * (int64_t)N,
+    tile_skewer<COMP, MAXQ, AVG, true>(L, L.rho + sk * (int64_t)N, L.vpec + sk * (int64_t)N,
                             L.temp ? L.temp + sk * (int64_t)N : nullptr, out, smem_raw, warp_tot, tile_hist,
                             whole_block());
 }
@@ -675,6 +816,7 @@ __global__ void __launch_bounds__(serve::kTauThreads, 1) tau_serve_kernel(unsign
 
 int block_threads(int n_pix)
 {
+    if (n_pix > 4096) return 1024;
     if (n_pix >= 2048) return 512;
     if (n_pix >= 512) return 256;
     return 128;
@@ -696,14 +838,14 @@ size_t tau_smem_bytes(int n_pix, int w_max, int precision)
 }
 
 template <typename K>
-static cudaError_t launch_kernel(K kernel, const TauLaunch& L, size_t smem, cudaStream_t stream)
+static cudaError_t launch_kernel(K kernel, const TauLaunch& L, size_t smem, int nt, cudaStream_t stream)
 {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     if (L.n_rows == 0) return cudaSuccess;
-    kernel<<<(unsigned)L.n_rows, block_threads(L.n_pix), smem, stream>>>(L);
+    kernel<<<(unsigned)L.n_rows, nt, smem, stream>>>(L);
     count_launch();
     return cudaGetLastError();
 }
@@ -712,11 +854,11 @@ template <bool COMP, bool AVG>
 static cudaError_t launch_tile_profile(const TauLaunch& L, cudaStream_t stream)
 {
     const size_t smem = tile_smem_bytes(L.n_pix, L.w_max);
-    const int nt = block_threads(L.n_pix);
+    const int nt = block_threads(L.n_pix);                   // N <= 8 nt (n_pix <= 8192)
     const int q = (L.n_pix + nt - 1) / nt;
-    if (q <= 4) return launch_kernel(tau_tile_kernel<COMP, 4, AVG>, L, smem, stream);
-    if (q <= 8) return launch_kernel(tau_tile_kernel<COMP, 8, AVG>, L, smem, stream);
-    return launch_kernel(tau_tile_kernel<COMP, 16, AVG>, L, smem, stream);
+    if (nt > 512) return launch_kernel(tau_tile_kernel<COMP, 8, AVG, 1024>, L, smem, nt, stream);
+    if (q <= 4) return launch_kernel(tau_tile_kernel<COMP, 4, AVG, 512>, L, smem, nt, stream);
+    return launch_kernel(tau_tile_kernel<COMP, 8, AVG, 512>, L, smem, nt, stream);
 }
 
 template <bool COMP>
@@ -732,7 +874,8 @@ cudaError_t launch_tau(const TauLaunch& L, int precision, cudaStream_t stream)
     case LYA_PREC_F32_COMPENSATED: return launch_tile<true>(L, stream);
     case LYA_PREC_F32_NAIVE: return launch_tile<false>(L, stream);
     case LYA_PREC_F64:
-        return launch_kernel(tau_kernel<LYA_PREC_F64>, L, global_smem_bytes(L.n_pix), stream);
+        return launch_kernel(tau_kernel<LYA_PREC_F64>, L, global_smem_bytes(L.n_pix),
+                             std::min(block_threads(L.n_pix), 512), stream);
     default: return cudaErrorInvalidValue;
     }
 }
