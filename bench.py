@@ -45,8 +45,8 @@ ALG_BYTES_PER_PX = 16          # rho, vpec, T read (12 B) + tau written (4 B)
 # scaled by the number of skewers, with the SHA-1 of the kernel source each
 # was taken on: reported as null once paper_1105_4747_gb300/csrc/tau_extract.cu
 # differs from it.
-TAU_DRAM_PROFILE = {"gpc": ((402.719744e6 + 75.848960e6) / 8192, "98c28325945f533e27dd4f697c35075f0fca4c56"),
-                    "grid1536": ((2.416009e9 + 0.744351e9) / 131072, "98c28325945f533e27dd4f697c35075f0fca4c56")}
+TAU_DRAM_PROFILE = {"gpc": ((402.740480e6 + 75.112192e6) / 8192, "3eac7d1f1584c2524068492618569c50211111dc"),
+                    "grid1536": ((2.416990e9 + 0.744570880e9) / 131072, "3eac7d1f1584c2524068492618569c50211111dc")}
 
 
 def workload_config(spec, S, extra=None, grid=False):

@@ -483,11 +483,39 @@ __device__ __forceinline__ void pair4_segment(const float4* __restrict__ rec, in
         }
     };
     int k = k0;
-    if constexpr (COMP) {
+    if constexpr (AVG) {
+        // the cell averages keep fewer terms in flight (four erfc each)
         while (k < k1) {
             float P[4] = {0.f, 0.f, 0.f, 0.f};
-            const int kk = min(k + 4, k1);
+            const int kk = COMP ? min(k + 4, k1) : k1;
             for (; k < kk; ++k) {
+                float t[4];
+                terms(rec[k], t);
+#pragma unroll
+                for (int m = 0; m < 4; ++m) P[m] += t[m];
+            }
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                if constexpr (COMP) kahan_fold(S[m], C[m], P[m]);
+                else S[m] += P[m];
+            }
+        }
+    } else if constexpr (COMP) {
+        // blocks of four candidates, read together and summed plainly, then
+        // folded into the Kahan sums; the last block may be short
+        for (; k + 4 <= k1; k += 4) {
+            const float4 r0 = rec[k], r1 = rec[k + 1], r2 = rec[k + 2], r3 = rec[k + 3];
+            float t0[4], t1[4], t2[4], t3[4];
+            terms(r0, t0);
+            terms(r1, t1);
+            terms(r2, t2);
+            terms(r3, t3);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) kahan_fold(S[m], C[m], (t0[m] + t1[m]) + (t2[m] + t3[m]));
+        }
+        if (k < k1) {
+            float P[4] = {0.f, 0.f, 0.f, 0.f};
+            for (; k < k1; ++k) {
                 float t[4];
                 terms(rec[k], t);
 #pragma unroll
