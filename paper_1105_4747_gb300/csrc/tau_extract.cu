@@ -1,10 +1,11 @@
 // tau_extract.cu -- optical depth along skewers (Eq. 4-6), sm_103a.
 //
 // Three kernels:
-//   * tau_tile_kernel (FP32, the product path): one CTA per skewer; sources
-//     counting-sorted by target pixel; four lanes share an eight-pixel tile,
-//     taken in order of candidate count, and sum the sources whose reach
-//     covers the tile (compensated or plain);
+//   * tau_tile_kernel (FP32, the product path): one CTA per skewer (1,024
+//     threads above 4,096 pixels, else 512 or fewer); sources counting-sorted
+//     by target pixel; four lanes share an eight-pixel tile (two lanes of four
+//     pixels where the runs are long), taken in order of candidate count, and
+//     sum the sources whose reach covers the tile (compensated or plain);
 //   * tau_serve_kernel (the serving loop): the same per-skewer body run by
 //     1 to 8 warp groups of a persistent 1024-thread CTA over a work list;
 //   * tau_kernel (FP64 comparator): one CTA per skewer; sources
@@ -269,7 +270,9 @@ __global__ void __launch_bounds__(512) tau_kernel(const TauLaunch L)
 // rounds), so the lanes of a warp walk lists of nearly equal length.  Four
 // lanes share a tile and each owns two adjacent pixels: a candidate record is
 // read once from shared memory and evaluated for both (one MUFU ex2 each).
-// tau is gathered in shared memory and written to HBM in order at the end.
+// Where the runs average kLongRun candidates or more, two lanes share a tile
+// with four pixels each.  tau is gathered in shared memory and written to HBM
+// in order at the end.
 //
 // Accumulation per pixel: the terms of four consecutive candidates are added
 // plainly, then folded into a Kahan sum (compensated variant); or every term
