@@ -45,8 +45,24 @@ ALG_BYTES_PER_PX = 16          # rho, vpec, T read (12 B) + tau written (4 B)
 # scaled by the number of skewers, with the SHA-1 of the kernel source each
 # was taken on: reported as null once paper_1105_4747_gb300/csrc/tau_extract.cu
 # differs from it.
-TAU_DRAM_PROFILE = {"gpc": ((402.740480e6 + 75.112192e6) / 8192, "3eac7d1f1584c2524068492618569c50211111dc"),
-                    "grid1536": ((2.416990e9 + 0.744570880e9) / 131072, "3eac7d1f1584c2524068492618569c50211111dc")}
+TAU_DRAM_PROFILE = {"gpc": ((402.740480e6 + 75.112192e6) / 8192, "1a6aa4c2d55139081b5e4f0e8a903b56bd3b81c3"),
+                    "grid1536": ((2.416990e9 + 0.744570880e9) / 131072, "1a6aa4c2d55139081b5e4f0e8a903b56bd3b81c3")}
+
+
+def tau_code_hash() -> str:
+    """SHA-1 of the optical-depth kernel's code: tau_extract.cu and the headers
+    it includes, with comments and blank lines removed (a comment edit does not
+    change the kernel whose DRAM traffic was captured)."""
+    import hashlib
+    import re
+    csrc = os.path.join(ROOT, "paper_1105_4747_gb300", "csrc")
+    h = hashlib.sha1()
+    for name in ("tau_extract.cu", "lya_device.cuh", "lya_internal.h", "serve_internal.h"):
+        txt = open(os.path.join(csrc, name)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        txt = re.sub(r"//[^\n]*", "", txt)
+        h.update("\n".join(line.rstrip() for line in txt.splitlines() if line.strip()).encode())
+    return h.hexdigest()
 
 
 def workload_config(spec, S, extra=None, grid=False):
@@ -598,10 +614,8 @@ def run_ours(args):
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     achieved = ALG_BYTES_PER_PX * n_px / (tau_ms / 1e3) / 1e9
-    import hashlib
-    src = os.path.join(ROOT, "paper_1105_4747_gb300", "csrc", "tau_extract.cu")
-    per_skewer, profiled_sha = TAU_DRAM_PROFILE[args.workload]
-    same_kernel = hashlib.sha1(open(src, "rb").read()).hexdigest() == profiled_sha
+    per_skewer, profiled_hash = TAU_DRAM_PROFILE[args.workload]
+    same_kernel = tau_code_hash() == profiled_hash
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak,
                 "traffic": per_skewer * S if same_kernel else None,
