@@ -304,6 +304,8 @@ __host__ __device__ inline size_t tile_smem_bytes(int n_pix, int w_max)
 // scratch and the tile-order histogram.
 constexpr int kGroupScanInts = 36;
 constexpr int kRunTotal = 34;                    // scan scratch slot: the skewer's summed tile runs
+constexpr int kSkewerReach = 35;                 // scan scratch slot: the skewer's widest reach h
+constexpr int kLocalReach = 64;                  // window bound up to which tiles search their runs locally
 constexpr int kLongRun = 256;                    // mean run per tile from which a lane takes four pixels
 __host__ __device__ inline size_t group_smem_bytes(int n_pix, int w_max)
 {
@@ -351,6 +353,47 @@ __device__ __forceinline__ int last_at_most(const int* v, int a, int b, int x)
     return lo - 1;
 }
 
+// Local candidate runs.  hm[t] is the widest reach of the sources in bin t
+// (-1: empty).  The first bin t in [lo - hs, lo) whose sources reach pixel
+// lo (t + hm[t] >= lo), else lo; the last bin t in (hi, hi + hs] whose
+// sources reach hi (t - hm[t] <= hi), else hi.  Bins past the seam are read
+// at their periodic image.  With N a multiple of 4 the bins are read four at
+// a time (16-byte aligned groups).
+__device__ __forceinline__ int local_run_left(const int* hm, int N, int lo, int hs, bool vec)
+{
+    if (vec) {
+        for (int g = (lo - hs) & ~3; g < lo; g += 4) {
+            const int4 q = *reinterpret_cast<const int4*>(hm + (g < 0 ? g + N : g));
+            const int t0 = max(g, lo - hs);
+            if (g >= t0 && g + q.x >= lo) return g;
+            if (g + 1 >= t0 && g + 1 < lo && g + 1 + q.y >= lo) return g + 1;
+            if (g + 2 >= t0 && g + 2 < lo && g + 2 + q.z >= lo) return g + 2;
+            if (g + 3 >= t0 && g + 3 < lo && g + 3 + q.w >= lo) return g + 3;
+        }
+        return lo;
+    }
+    for (int t = lo - hs; t < lo; ++t)
+        if (t + hm[t < 0 ? t + N : t] >= lo) return t;
+    return lo;
+}
+__device__ __forceinline__ int local_run_right(const int* hm, int N, int hi, int hs, bool vec)
+{
+    if (vec) {
+        for (int g = (hi + hs) & ~3; g + 3 > hi; g -= 4) {
+            const int4 q = *reinterpret_cast<const int4*>(hm + (g >= N ? g - N : g));
+            const int t1 = hi + hs;
+            if (g + 3 <= t1 && g + 3 > hi && g + 3 - q.w <= hi) return g + 3;
+            if (g + 2 <= t1 && g + 2 > hi && g + 2 - q.z <= hi) return g + 2;
+            if (g + 1 <= t1 && g + 1 > hi && g + 1 - q.y <= hi) return g + 1;
+            if (g <= t1 && g > hi && g - q.x <= hi) return g;
+        }
+        return hi;
+    }
+    for (int t = hi + hs; t > hi; --t)
+        if (t - hm[t >= N ? t - N : t] <= hi) return t;
+    return hi;
+}
+
 __device__ __forceinline__ void kahan_fold(float& S, float& C, float P)
 {
     const float y = __fsub_rn(P, C);
@@ -387,7 +430,31 @@ __device__ __forceinline__ void pair2_segment(const float4* __restrict__ rec, in
         }
     };
     int k = k0;
-    if constexpr (COMP) {
+    if constexpr (COMP && !AVG) {
+        // blocks of four candidates read together, their terms summed plainly
+        // and the block sums folded into the Kahan sums; the last block may be short
+        for (; k + 4 <= k1; k += 4) {
+            const float4 r0 = rec[k], r1 = rec[k + 1], r2 = rec[k + 2], r3 = rec[k + 3];
+            float a0, a1, b0, b1, c0, c1, d0, d1;
+            terms(r0, a0, a1);
+            terms(r1, b0, b1);
+            terms(r2, c0, c1);
+            terms(r3, d0, d1);
+            kahan_fold(S[0], C[0], (a0 + b0) + (c0 + d0));
+            kahan_fold(S[1], C[1], (a1 + b1) + (c1 + d1));
+        }
+        if (k < k1) {
+            float P0 = 0.f, P1 = 0.f;
+            for (; k < k1; ++k) {
+                float t0, t1;
+                terms(rec[k], t0, t1);
+                P0 += t0;
+                P1 += t1;
+            }
+            kahan_fold(S[0], C[0], P0);
+            kahan_fold(S[1], C[1], P1);
+        }
+    } else if constexpr (COMP) {
         while (k < k1) {
             float P0 = 0.f, P1 = 0.f;
             const int kk = min(k + 4, k1);
@@ -614,16 +681,28 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
             T_[q] = (j < N && temp) ? __ldcs(temp + j) : 0.f;
         }
     }
+    // local: every tile finds its run by looking at most the skewer's widest
+    // reach to either side in a per-bin widest-reach array (-1: empty bin);
+    // otherwise the runs come from block-wide envelope scans
+    const bool local = Wd <= kLocalReach;
     for (int k = tid - 4; k < N; k += nt) cnt[k] = 0;
-    for (int e = tid; e < NE; e += nt) reach[e] = kReachLow;
+    if (local) {
+        for (int e = tid; e < N; e += nt) reach[e] = -1;
+    } else {
+        for (int e = tid; e < NE; e += nt) reach[e] = kReachLow;
+    }
     for (int k = tid; k < kTileKeys; k += nt) tile_hist[k] = 0;
-    if (tid == 0) warp_tot[kRunTotal] = 0;
+    if (tid == 0) {
+        warp_tot[kRunTotal] = 0;
+        warp_tot[kSkewerReach] = 0;
+    }
     g.sync();
 
     // 2. per-source constants (kept in registers) and the histogram of target
     //    pixels; th_ packs (target << 16) | reach, -1 = no source
     float a_[MAXQ], bb_[MAXQ], w_[MAXQ];
     int th_[MAXQ];
+    int hsk = 0;
 #pragma unroll
     for (int q = 0; q < MAXQ; ++q) {
         const int j = src_index(q, vec, tid, nt);
@@ -643,7 +722,15 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
             w_[q] = s.w;
             th_[q] = (s.t << 16) | s.h;
             atomicAdd(&cnt[s.t], 1);
+            if (local) {
+                atomicMax(&reach[s.t], s.h);
+                hsk = max(hsk, s.h);
+            }
         }
+    }
+    if (local) {
+        hsk = __reduce_max_sync(0xffffffffu, hsk);
+        if ((tid & 31) == 0 && hsk > 0) atomicMax(&warp_tot[kSkewerReach], hsk);
     }
     g.sync();
 
@@ -657,40 +744,42 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
         const int pos = atomicAdd(&cnt[t], 1);
         if (pos >= N) { atomicOr(L.err, 2); th_[q] = -1; continue; }   // input changed under the kernel
         rec[pos] = make_float4(a_[q], bb_[q], w_[q], (float)t);
+        if (local) continue;
         atomicMax(&reach[t + Wd], t + h);
         if (t >= N - Wd) atomicMax(&reach[t - N + Wd], t - N + h);
         if (t < Wd) atomicMax(&reach[t + N + Wd], t + N + h);
     }
     g.sync();
-
-    // 4. first candidate bin of every tile: search the prefix max of the right reach
-    block_prefix_max(reach, NE, warp_tot, kReachLow, g);       // ends with a barrier
-    for (int tile = tid; tile < NT; tile += nt) {
-        const int lo = kTile * tile, hi = min(lo + kTile - 1, N - 1);
-        const int e = first_at_least(reach, lo, min(hi + 2 * Wd, NE - 1), lo);
-        Lt[tile] = (short)(e <= min(hi + 2 * Wd, NE - 1) ? e - Wd : kEmptyRun);
-    }
-    g.sync();
-    for (int e = tid; e < NE; e += nt) reach[e] = kReachHigh;
-    g.sync();
+    if (!local) {
+        // 4. first candidate bin of every tile: search the prefix max of the right reach
+        block_prefix_max(reach, NE, warp_tot, kReachLow, g);       // ends with a barrier
+        for (int tile = tid; tile < NT; tile += nt) {
+            const int lo = kTile * tile, hi = min(lo + kTile - 1, N - 1);
+            const int e = first_at_least(reach, lo, min(hi + 2 * Wd, NE - 1), lo);
+            Lt[tile] = (short)(e <= min(hi + 2 * Wd, NE - 1) ? e - Wd : kEmptyRun);
+        }
+        g.sync();
+        for (int e = tid; e < NE; e += nt) reach[e] = kReachHigh;
+        g.sync();
 #pragma unroll
-    for (int q = 0; q < MAXQ; ++q) {
-        if (th_[q] < 0) continue;
-        const int t = th_[q] >> 16, h = th_[q] & 0xffff;
-        atomicMin(&reach[t + Wd], t - h);
-        if (t >= N - Wd) atomicMin(&reach[t - N + Wd], t - N - h);
-        if (t < Wd) atomicMin(&reach[t + N + Wd], t + N - h);
-    }
-    g.sync();
+        for (int q = 0; q < MAXQ; ++q) {
+            if (th_[q] < 0) continue;
+            const int t = th_[q] >> 16, h = th_[q] & 0xffff;
+            atomicMin(&reach[t + Wd], t - h);
+            if (t >= N - Wd) atomicMin(&reach[t - N + Wd], t - N - h);
+            if (t < Wd) atomicMin(&reach[t + N + Wd], t + N - h);
+        }
+        g.sync();
 
-    // 5. last candidate bin of every tile: search the suffix min of the left reach
-    block_suffix_min(reach, NE, warp_tot, kReachHigh, g);      // ends with a barrier
-    for (int tile = tid; tile < NT; tile += nt) {
-        const int lo = kTile * tile, hi = min(lo + kTile - 1, N - 1);
-        const int e = last_at_most(reach, lo, min(hi + 2 * Wd, NE - 1), hi);
-        Rt[tile] = (short)(e >= lo ? e - Wd : -kEmptyRun);
+        // 5. last candidate bin of every tile: search the suffix min of the left reach
+        block_suffix_min(reach, NE, warp_tot, kReachHigh, g);      // ends with a barrier
+        for (int tile = tid; tile < NT; tile += nt) {
+            const int lo = kTile * tile, hi = min(lo + kTile - 1, N - 1);
+            const int e = last_at_most(reach, lo, min(hi + 2 * Wd, NE - 1), hi);
+            Rt[tile] = (short)(e >= lo ? e - Wd : -kEmptyRun);
+        }
+        g.sync();
     }
-    g.sync();
 
     // 6. tiles ordered by candidate count, largest first (counting sort)
     constexpr int kMaxTilesPerThread = (MAXQ + kTile - 1) / kTile;   // NT <= MAXQ nt / kTile
@@ -701,8 +790,23 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
         const int tile = tid + u * nt;
         tkey[u] = -1;
         if (tile < NT) {
+            int lx, rx;
+            if (local) {
+                // first bin at most hs left of the tile whose widest source
+                // reaches it, last bin at most hs right of it likewise (bins
+                // past the seam are read at their periodic image)
+                const int lo = kTile * tile, hi = min(lo + kTile - 1, N - 1);
+                const int hs = warp_tot[kSkewerReach];
+                lx = local_run_left(reach, N, lo, hs, vec);
+                rx = local_run_right(reach, N, hi, hs, vec);
+                Lt[tile] = (short)lx;
+                Rt[tile] = (short)rx;
+            } else {
+                lx = Lt[tile];
+                rx = Rt[tile];
+            }
             int c = 0;
-            for_tile_run(bin, N, Lt[tile], Rt[tile], [&](int k0, int k1, float) { c += k1 - k0; });
+            for_tile_run(bin, N, lx, rx, [&](int k0, int k1, float) { c += k1 - k0; });
             tkey[u] = kTileKeys - 1 - min(c, kTileKeys - 1);
             atomicAdd(&tile_hist[tkey[u]], 1);
             runs += c;
