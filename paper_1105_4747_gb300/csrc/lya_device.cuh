@@ -38,6 +38,14 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
+// Bulk prefetch of bytes (a multiple of 16) at a 16-byte aligned global
+// address into L2 (PTX cp.async.bulk.prefetch.L2): no registers, no shared
+// memory, no completion to wait for.
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // Kahan-compensated FP32 accumulator.  The adds are written with explicit
 // round-to-nearest intrinsics so the compiler can neither contract nor
 // reassociate them.

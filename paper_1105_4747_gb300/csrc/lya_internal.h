@@ -39,6 +39,7 @@ struct TauLaunch {
     const int64_t* ids;       // nullptr: row r is skewer r
     int64_t n_rows;           // skewers to extract (grid size)
     int64_t n_skewers;        // skewers in the field (id bound)
+    int64_t pf_ahead;         // tile kernel: CTA r prefetches row r + pf_ahead into L2 (0: none)
     int n_pix;
     float* tau_out;           // [n_rows][n_pix]
     int* err;                 // device error word: bit 0 = skewer id out of range

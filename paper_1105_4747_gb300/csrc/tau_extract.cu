@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(512) tau_kernel(const TauLaunch L)
 // w_max; later tau) | tile runs L, R and the tile order (int16).
 constexpr int kTile = 8;
 constexpr int kLanesPerTile = 4;                 // each lane: kTile / kLanesPerTile = 2 pixels
-constexpr int kTileKeys = 256;                   // tile-order histogram (counts >= 255 share a key)
+constexpr int kTileKeys = 256;                   // tile-order histogram (counts >= 255 share a key; 8 per lane of one warp)
 constexpr int kReachLow = -(1 << 28);
 constexpr int kReachHigh = 1 << 28;
 constexpr int kEmptyRun = 30000;                 // L of a tile no source reaches (L > R)
@@ -444,12 +444,25 @@ __device__ __forceinline__ void pair2_segment(const float4* __restrict__ rec, in
             kahan_fold(S[1], C[1], (a1 + b1) + (c1 + d1));
         }
         if (k < k1) {
-            float P0 = 0.f, P1 = 0.f;
-            for (; k < k1; ++k) {
-                float t0, t1;
-                terms(rec[k], t0, t1);
-                P0 += t0;
-                P1 += t1;
+            // one to three left: a pair, then a single, without a loop
+            float P0, P1;
+            if (k + 2 <= k1) {
+                const float4 r0 = rec[k], r1 = rec[k + 1];
+                float a0, a1, b0, b1;
+                terms(r0, a0, a1);
+                terms(r1, b0, b1);
+                P0 = a0 + b0;
+                P1 = a1 + b1;
+                k += 2;
+            } else {
+                P0 = 0.f;
+                P1 = 0.f;
+            }
+            if (k < k1) {
+                float a0, a1;
+                terms(rec[k], a0, a1);
+                P0 += a0;
+                P1 += a1;
             }
             kahan_fold(S[0], C[0], P0);
             kahan_fold(S[1], C[1], P1);
@@ -685,13 +698,20 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
     // reach to either side in a per-bin widest-reach array (-1: empty bin);
     // otherwise the runs come from block-wide envelope scans
     const bool local = Wd <= kLocalReach;
-    for (int k = tid - 4; k < N; k += nt) cnt[k] = 0;
-    if (local) {
+    if (vec) {
+        // cnt[-4 .. N) and reach[0 .. N) are 16-byte aligned runs of whole int4s
+        for (int k = tid; k < N / 4 + 1; k += nt) reinterpret_cast<int4*>(cnt - 4)[k] = make_int4(0, 0, 0, 0);
+    } else {
+        for (int k = tid - 4; k < N; k += nt) cnt[k] = 0;
+    }
+    if (local && vec) {
+        for (int e = tid; e < N / 4; e += nt) reinterpret_cast<int4*>(reach)[e] = make_int4(-1, -1, -1, -1);
+    } else if (local) {
         for (int e = tid; e < N; e += nt) reach[e] = -1;
     } else {
         for (int e = tid; e < NE; e += nt) reach[e] = kReachLow;
     }
-    for (int k = tid; k < kTileKeys; k += nt) tile_hist[k] = 0;
+    for (int k = tid; k < kTileKeys / 4; k += nt) reinterpret_cast<int4*>(tile_hist)[k] = make_int4(0, 0, 0, 0);
     if (tid == 0) {
         warp_tot[kRunTotal] = 0;
         warp_tot[kSkewerReach] = 0;
@@ -814,7 +834,19 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
     }
     if (runs) atomicAdd(&warp_tot[kRunTotal], runs);
     g.sync();
-    block_exclusive_scan(tile_hist, kTileKeys, warp_tot, g);
+    if (tid < 32) {
+        // exclusive scan of the kTileKeys counts by the first warp, eight per lane
+        int4* h4 = reinterpret_cast<int4*>(tile_hist) + 2 * tid;
+        const int4 x = h4[0], y = h4[1];
+        const int loc = (x.x + x.y + x.z + x.w) + (y.x + y.y + y.z + y.w);
+        int run = warp_inclusive_scan(loc) - loc;
+        int4 ox, oy;
+        ox.x = run; run += x.x; ox.y = run; run += x.y; ox.z = run; run += x.z; ox.w = run; run += x.w;
+        oy.x = run; run += y.x; oy.y = run; run += y.y; oy.z = run; run += y.z; oy.w = run;
+        h4[0] = ox;
+        h4[1] = oy;
+    }
+    g.sync();
 #pragma unroll
     for (int u = 0; u < kMaxTilesPerThread; ++u)
         if (tkey[u] >= 0) order[atomicAdd(&tile_hist[tkey[u]], 1)] = (short)(tid + u * nt);
@@ -877,6 +909,19 @@ __global__ void __launch_bounds__(NTB, NTB >= 1024 ? 1 : 2) tau_tile_kernel(cons
         for (int i = threadIdx.x; i < N; i += blockDim.x) out[i] = 0.f;
         if (threadIdx.x == 0) atomicOr(L.err, 1);
         return;
+    }
+    if (threadIdx.x == 0 && L.pf_ahead > 0 && row + L.pf_ahead < L.n_rows) {
+        // the row a CTA about one wave later extracts, into L2: its loads then
+        // wait on L2 rather than HBM
+        const int64_t pr = row + L.pf_ahead;
+        const int64_t psk = L.ids ? L.ids[pr] : pr;
+        const unsigned bytes = 4u * (unsigned)N;
+        if (psk >= 0 && psk < L.n_skewers && (bytes & 15u) == 0) {
+            const float* rows[3] = {L.rho + psk * (int64_t)N, L.vpec + psk * (int64_t)N,
+                                    L.temp ? L.temp + psk * (int64_t)N : nullptr};
+            for (const float* q : rows)
+                if (q && (reinterpret_cast<uintptr_t>(q) & 15) == 0) prefetch_l2(q, bytes);
+        }
     }
     tile_skewer<COMP, MAXQ, AVG, true>(L, L.rho + sk * (int64_t)N, L.vpec + sk * (int64_t)N,
                             L.temp ? L.temp + sk * (int64_t)N : nullptr, out, smem_raw, warp_tot, tile_hist,
@@ -973,13 +1018,25 @@ size_t tau_smem_bytes(int n_pix, int w_max, int precision)
 }
 
 template <typename K>
-static cudaError_t launch_kernel(K kernel, const TauLaunch& L, size_t smem, int nt, cudaStream_t stream)
+static cudaError_t launch_kernel(K kernel, const TauLaunch& L0, size_t smem, int nt, cudaStream_t stream,
+                                 bool prefetch = false)
 {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
-    if (L.n_rows == 0) return cudaSuccess;
+    if (L0.n_rows == 0) return cudaSuccess;
+    TauLaunch L = L0;
+    L.pf_ahead = 0;
+    if (prefetch) {
+        // one wave ahead: the CTAs resident on the whole device at once
+        int dev = 0, sms = 0, per_sm = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, nt, smem) == cudaSuccess)
+            L.pf_ahead = (int64_t)sms * per_sm;
+        (void)cudaGetLastError();
+    }
     kernel<<<(unsigned)L.n_rows, nt, smem, stream>>>(L);
     count_launch();
     return cudaGetLastError();
@@ -991,9 +1048,9 @@ static cudaError_t launch_tile_profile(const TauLaunch& L, cudaStream_t stream)
     const size_t smem = tile_smem_bytes(L.n_pix, L.w_max);
     const int nt = block_threads(L.n_pix);                   // N <= 8 nt (n_pix <= 8192)
     const int q = (L.n_pix + nt - 1) / nt;
-    if (nt > 512) return launch_kernel(tau_tile_kernel<COMP, 8, AVG, 1024>, L, smem, nt, stream);
-    if (q <= 4) return launch_kernel(tau_tile_kernel<COMP, 4, AVG, 512>, L, smem, nt, stream);
-    return launch_kernel(tau_tile_kernel<COMP, 8, AVG, 512>, L, smem, nt, stream);
+    if (nt > 512) return launch_kernel(tau_tile_kernel<COMP, 8, AVG, 1024>, L, smem, nt, stream, true);
+    if (q <= 4) return launch_kernel(tau_tile_kernel<COMP, 4, AVG, 512>, L, smem, nt, stream, true);
+    return launch_kernel(tau_tile_kernel<COMP, 8, AVG, 512>, L, smem, nt, stream, true);
 }
 
 template <bool COMP>
