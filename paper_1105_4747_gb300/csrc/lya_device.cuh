@@ -99,8 +99,11 @@ __device__ __forceinline__ int scan_chunk(int n, int nt) { return ((n + nt - 1) 
 // In-place exclusive scan of data[0..n) (ints in shared memory) by the
 // group; returns the total on every thread.  warp_tot holds >= 33 ints of
 // shared scratch private to the group.  Synchronises the group: call from
-// all of its threads.
-__device__ inline int block_exclusive_scan(int* data, int n, int* warp_tot, const Group& g)
+// all of its threads.  With marks (indices into data, -1 for none) and
+// mark_out, the scanned values at those indices are also left in
+// mark_out[0], mark_out[1] by the time the scan returns.
+__device__ inline int block_exclusive_scan(int* data, int n, int* warp_tot, const Group& g,
+                                           int mark_a = -1, int mark_b = -1, int* mark_out = nullptr)
 {
     const int nt = g.nt;
     const int tid = g.tid;
@@ -124,6 +127,10 @@ __device__ inline int block_exclusive_scan(int* data, int n, int* warp_tot, cons
         int c = data[k];
         data[k] = run;
         run += c;
+    }
+    if (mark_out) {
+        if (mark_a >= lo && mark_a < hi) mark_out[0] = data[mark_a];
+        if (mark_b >= lo && mark_b < hi) mark_out[1] = data[mark_b];
     }
     int total = warp_tot[32];
     g.sync();

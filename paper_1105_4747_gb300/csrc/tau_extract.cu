@@ -3,9 +3,10 @@
 // Three kernels:
 //   * tau_tile_kernel (FP32, the product path): one CTA per skewer (1,024
 //     threads above 4,096 pixels, else 512 or fewer); sources counting-sorted
-//     by target pixel; four lanes share an eight-pixel tile (two lanes of four
-//     pixels where the runs are long), taken in order of candidate count, and
-//     sum the sources whose reach covers the tile (compensated or plain);
+//     by target pixel; each eight-pixel tile finds the run of sources whose
+//     reach covers it; four lanes share a tile (two lanes of four pixels
+//     where the runs are long), taken in order of run length, and sum the
+//     run (compensated or plain);
 //   * tau_serve_kernel (the serving loop): the same per-skewer body run by
 //     1 to 8 warp groups of a persistent 1024-thread CTA over a work list;
 //   * tau_kernel (FP64 comparator): one CTA per skewer; sources
@@ -256,14 +257,23 @@ __global__ void __launch_bounds__(512) tau_kernel(const TauLaunch L)
 // covers the pixels |i - t_j| <= h_j, h_j = floor((nsigma b_j + |r_j|)/du).
 // The output pixels are cut into tiles of kTile consecutive pixels; a tile's
 // candidate sources are the sorted run of target bins [L, R] with
-//   L = first bin t with max_{t' <= t}(t' + h_t') >= first pixel of the tile
-//   R = last  bin t with min_{t' >= t}(t' - h_t') <= last pixel of the tile
-// (prefix max of the right reach, suffix min of the left reach, over bins
-// extended by w_max on both sides so the periodic wrap is explicit).  Both
-// are monotone, and h <= w_max confines L and R of the tile at pixels
-// [lo, hi] to the extended bins [lo, hi + 2 w_max]: a binary search there
-// finds them.  The run holds every source covering the tile and, away from
-// the broadest lines, little else.
+//   L = first bin t whose widest source reaches the first pixel of the tile
+//       (t + h_t >= lo, h_t the widest reach in bin t)
+//   R = last bin t whose widest source reaches the last pixel (t - h_t <= hi).
+// The run holds every source covering the tile and, away from the broadest
+// lines, little else.  Two ways to find L and R:
+//   * local (window bound w_max <= kLocalReach): a per-bin widest-reach array
+//     filled with shared-memory atomics; each tile scans at most the skewer's
+//     widest reach hs to either side of it, four bins per 16-byte read;
+//   * otherwise: the prefix max of the right reach and the suffix min of the
+//     left reach, over bins extended by w_max on both sides so the periodic
+//     wrap is explicit; both are monotone and a binary search over
+//     [lo, hi + 2 w_max] of the extended bins finds L and R.
+// With local runs the records of bins [N - hs, N) are also copied in front of
+// the sorted records (target t - N) and those of bins [0, hs) behind them
+// (t + N), so that every tile's run, across the seam or not, is one range of
+// the record array, stored beside the tile order (when the copies fit the
+// reserved ext_capacity records; else the run is split at the seam).
 //
 // Load balance: the tiles are counting-sorted by candidate count, largest
 // first, and handed to the threads in that order (reversed on alternate
@@ -274,13 +284,17 @@ __global__ void __launch_bounds__(512) tau_kernel(const TauLaunch L)
 // with four pixels each.  tau is gathered in shared memory and written to HBM
 // in order at the end.
 //
-// Accumulation per pixel: the terms of four consecutive candidates are added
-// plainly, then folded into a Kahan sum (compensated variant); or every term
-// is added plainly (naive variant).
+// Accumulation per pixel: the terms of four consecutive candidates (read
+// together) are added plainly, then folded into a Kahan sum (compensated
+// variant); or every term is added plainly (naive variant).
 //
-// Shared memory: records (N rounded up to 4) | bin counts (4 + N rounded up
-// to 4; the leading zero makes bin starts and ends one array) | reach (N + 2
-// w_max; later tau) | tile runs L, R and the tile order (int16).
+// Shared memory: records (N + ext_capacity rounded up to 4) | bin counts
+// (4 + N rounded up to 4; the leading zero makes bin starts and ends one
+// array) | reach (N + 2 w_max; later tau) | tile runs L, R, the tile order and
+// the ordered tiles' record ranges (int16).
+//
+// Each CTA of the standalone kernel also asks L2 for the inputs of the row one
+// wave of CTAs later (a bulk prefetch), so its loads wait on L2, not HBM.
 constexpr int kTile = 8;
 constexpr int kLanesPerTile = 4;                 // each lane: kTile / kLanesPerTile = 2 pixels
 constexpr int kTileKeys = 256;                   // tile-order histogram (counts >= 255 share a key; 8 per lane of one warp)
@@ -292,20 +306,32 @@ constexpr float kHalfSqrtPi = 0.88622692545275801f;
 
 __host__ __device__ __forceinline__ int round_up4(int n) { return (n + 3) & ~3; }
 
-// FP32 tile gather: records | bin starts | reach | tile runs.
+constexpr int kLocalReach = 64;                  // window bound up to which tiles search their runs locally
+
+// Records past the seam copied to the ends of the record array (local
+// searches only), so that every tile's candidates are one contiguous run:
+// room for four sources per bin within w_max + 4 of either end.
+__host__ __device__ __forceinline__ int ext_capacity(int w_max)
+{
+    return w_max <= kLocalReach ? 4 * (2 * w_max + 8) : 0;
+}
+
+// FP32 tile gather: records (with the seam copies) | bin starts | reach |
+// tile runs, tile order and the ordered tiles' record ranges.
 __host__ __device__ inline size_t tile_smem_bytes(int n_pix, int w_max)
 {
     const int nt = (n_pix + kTile - 1) / kTile;
-    return sizeof(float4) * (size_t)round_up4(n_pix) + sizeof(int) * (size_t)(4 + round_up4(n_pix)) +
-           sizeof(int) * (size_t)(n_pix + 2 * w_max) + 3 * sizeof(short) * (size_t)nt;
+    return sizeof(float4) * (size_t)round_up4(n_pix + ext_capacity(w_max)) +
+           sizeof(int) * (size_t)(4 + round_up4(n_pix)) + sizeof(int) * (size_t)(n_pix + 2 * w_max) +
+           5 * sizeof(short) * (size_t)nt;
 }
 
-// One warp group of the serving kernel: its tile arrays, then 36 ints of scan
+// One warp group of the serving kernel: its tile arrays, then 40 ints of scan
 // scratch and the tile-order histogram.
-constexpr int kGroupScanInts = 36;
+constexpr int kGroupScanInts = 40;
 constexpr int kRunTotal = 34;                    // scan scratch slot: the skewer's summed tile runs
 constexpr int kSkewerReach = 35;                 // scan scratch slot: the skewer's widest reach h
-constexpr int kLocalReach = 64;                  // window bound up to which tiles search their runs locally
+constexpr int kSeamStarts = 36;                  // scan scratch slots 36, 37: bin starts at N - h and h
 constexpr int kLongRun = 256;                    // mean run per tile from which a lane takes four pixels
 __host__ __device__ inline size_t group_smem_bytes(int n_pix, int w_max)
 {
@@ -620,7 +646,8 @@ __device__ __forceinline__ void pair4_segment(const float4* __restrict__ rec, in
 // Step 7 with two lanes per tile, four pixels each, over the tiles in order.
 template <bool COMP, bool AVG, int EXP>
 __device__ __forceinline__ void tiles_by_four(const float4* __restrict__ rec, const int* bin, const short* Lt,
-                                              const short* Rt, const short* order, int N, int NT, float K,
+                                              const short* Rt, const short* order, const short* ok0,
+                                              const short* ok1, bool ext, int N, int NT, float K,
                                               float* tau_s, int tid, int nt)
 {
     const int half = tid & 1, ng = nt / 2, grp = tid / 2;
@@ -630,9 +657,13 @@ __device__ __forceinline__ void tiles_by_four(const float4* __restrict__ rec, co
         const int tile = order[i];
         const int o = kTile * tile + 4 * half;
         float S[4] = {0.f, 0.f, 0.f, 0.f}, C[4] = {0.f, 0.f, 0.f, 0.f};
-        for_tile_run(bin, N, Lt[tile], Rt[tile], [&](int k0, int k1, float shift) {
-            pair4_segment<COMP, AVG, EXP>(rec, k0, k1, (float)o + shift, S, C);
-        });
+        if (ext) {
+            pair4_segment<COMP, AVG, EXP>(rec, ok0[i], ok1[i], (float)o, S, C);
+        } else {
+            for_tile_run(bin, N, Lt[tile], Rt[tile], [&](int k0, int k1, float shift) {
+                pair4_segment<COMP, AVG, EXP>(rec, k0, k1, (float)o + shift, S, C);
+            });
+        }
 #pragma unroll
         for (int m = 0; m < 4; ++m)
             if (o + m < N) tau_s[o + m] = K * (COMP ? __fsub_rn(S[m], C[m]) : S[m]);
@@ -655,8 +686,9 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
     const int NE = N + 2 * Wd;
     const int NT = (N + kTile - 1) / kTile;
     const int tid = g.tid, nt = g.nt;
-    float4* rec = reinterpret_cast<float4*>(smem);
-    int* cnt = reinterpret_cast<int*>(rec + round_up4(N)) + 4;   // N (padded to 4), cnt[-1] = 0
+    const int Cx = ext_capacity(Wd);
+    float4* rec = reinterpret_cast<float4*>(smem);               // N + Cx (padded to 4)
+    int* cnt = reinterpret_cast<int*>(rec + round_up4(N + Cx)) + 4;   // N (padded to 4), cnt[-1] = 0
     int* bin = cnt - 1;                                          // after the scatter: bin[t] = start(t),
                                                                  // bin[t + 1] = end(t)
     int* reach = cnt + round_up4(N);                         // NE; tau once the runs are known
@@ -664,6 +696,8 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
     short* Lt = reinterpret_cast<short*>(reach + NE);        // NT
     short* Rt = Lt + NT;                                     // NT
     short* order = Rt + NT;                                  // NT: tiles by candidate count
+    short* ok0 = order + NT;                                 // NT: record run of order[i] (seam copies)
+    short* ok1 = ok0 + NT;
 
     // 1. every input load issued up front (float4 when rows are 16-byte aligned)
     const bool vec = (N & 3) == 0;
@@ -755,15 +789,25 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
     g.sync();
 
     // 3. bin starts; scatter the records {a, c r, w, t} and every source's
-    //    right reach t + h (three periodic images)
-    block_exclusive_scan(cnt, N, warp_tot, g);
+    //    right reach t + h (three periodic images).  With local searches the
+    //    sources of bins [N - hs, N) are later copied in front of the records
+    //    (t - N) and those of bins [0, hs) behind them (t + N), so the
+    //    records start at P = the number of the former: ext (when the copies
+    //    fit the reserved Cx records)
+    const int hs = local ? warp_tot[kSkewerReach] : 0;
+    const int nsrc = block_exclusive_scan(cnt, N, warp_tot, g, hs > 0 ? N - hs : -1, hs > 0 ? hs : -1,
+                                          warp_tot + kSeamStarts);
+    const int P = hs > 0 ? nsrc - warp_tot[kSeamStarts] : 0;
+    const int npost = hs > 0 ? warp_tot[kSeamStarts + 1] : 0;
+    const bool ext = local && P + npost <= Cx;
+    const int base = ext ? P : 0;
 #pragma unroll
     for (int q = 0; q < MAXQ; ++q) {
         if (th_[q] < 0) continue;
         const int t = th_[q] >> 16, h = th_[q] & 0xffff;
         const int pos = atomicAdd(&cnt[t], 1);
         if (pos >= N) { atomicOr(L.err, 2); th_[q] = -1; continue; }   // input changed under the kernel
-        rec[pos] = make_float4(a_[q], bb_[q], w_[q], (float)t);
+        rec[base + pos] = make_float4(a_[q], bb_[q], w_[q], (float)t);
         if (local) continue;
         atomicMax(&reach[t + Wd], t + h);
         if (t >= N - Wd) atomicMax(&reach[t - N + Wd], t - N + h);
@@ -803,7 +847,7 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
 
     // 6. tiles ordered by candidate count, largest first (counting sort)
     constexpr int kMaxTilesPerThread = (MAXQ + kTile - 1) / kTile;   // NT <= MAXQ nt / kTile
-    int tkey[kMaxTilesPerThread];
+    int tkey[kMaxTilesPerThread], kk0[kMaxTilesPerThread], kk1[kMaxTilesPerThread];
     int runs = 0;
 #pragma unroll
     for (int u = 0; u < kMaxTilesPerThread; ++u) {
@@ -816,23 +860,45 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
                 // reaches it, last bin at most hs right of it likewise (bins
                 // past the seam are read at their periodic image)
                 const int lo = kTile * tile, hi = min(lo + kTile - 1, N - 1);
-                const int hs = warp_tot[kSkewerReach];
                 lx = local_run_left(reach, N, lo, hs, vec);
                 rx = local_run_right(reach, N, hi, hs, vec);
-                Lt[tile] = (short)lx;
-                Rt[tile] = (short)rx;
+                if (!ext) {
+                    Lt[tile] = (short)lx;
+                    Rt[tile] = (short)rx;
+                }
             } else {
                 lx = Lt[tile];
                 rx = Rt[tile];
             }
             int c = 0;
-            for_tile_run(bin, N, lx, rx, [&](int k0, int k1, float) { c += k1 - k0; });
+            if (ext) {
+                // the run as one range of the record array with its copies
+                kk0[u] = lx >= 0 ? base + bin[lx] : bin[lx + N] - (nsrc - P);
+                kk1[u] = rx < N ? base + bin[rx + 1] : base + nsrc + bin[rx - N + 1];
+                c = kk1[u] - kk0[u];
+            } else {
+                for_tile_run(bin, N, lx, rx, [&](int k0, int k1, float) { c += k1 - k0; });
+            }
             tkey[u] = kTileKeys - 1 - min(c, kTileKeys - 1);
             atomicAdd(&tile_hist[tkey[u]], 1);
             runs += c;
         }
     }
     if (runs) atomicAdd(&warp_tot[kRunTotal], runs);
+    if (ext) {
+        // the seam copies: bins [N - hs, N) in front as t - N, bins [0, hs) behind as t + N
+        for (int e = tid; e < P + npost; e += nt) {
+            if (e < P) {
+                float4 r = rec[base + nsrc - P + e];
+                r.w -= (float)N;
+                rec[e] = r;
+            } else {
+                float4 r = rec[base + e - P];
+                r.w += (float)N;
+                rec[base + nsrc + e - P] = r;
+            }
+        }
+    }
     g.sync();
     if (tid < 32) {
         // exclusive scan of the kTileKeys counts by the first warp, eight per lane
@@ -848,8 +914,15 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
     }
     g.sync();
 #pragma unroll
-    for (int u = 0; u < kMaxTilesPerThread; ++u)
-        if (tkey[u] >= 0) order[atomicAdd(&tile_hist[tkey[u]], 1)] = (short)(tid + u * nt);
+    for (int u = 0; u < kMaxTilesPerThread; ++u) {
+        if (tkey[u] < 0) continue;
+        const int pos = atomicAdd(&tile_hist[tkey[u]], 1);
+        order[pos] = (short)(tid + u * nt);
+        if (ext) {
+            ok0[pos] = (short)kk0[u];
+            ok1[pos] = (short)kk1[u];
+        }
+    }
     g.sync();
 
     // 7. lane groups walk the tiles in that order (reversed on alternate
@@ -860,13 +933,15 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
     if (ALT_EXP && L.exp_method != LYA_EXP_MUFU) {
         if constexpr (ALT_EXP && !AVG) {
             if (L.exp_method == LYA_EXP_RECURRENCE)
-                tiles_by_four<COMP, false, LYA_EXP_RECURRENCE>(rec, bin, Lt, Rt, order, N, NT, K, tau_s, tid, nt);
+                tiles_by_four<COMP, false, LYA_EXP_RECURRENCE>(rec, bin, Lt, Rt, order, ok0, ok1, ext, N, NT, K,
+                                                               tau_s, tid, nt);
             else
-                tiles_by_four<COMP, false, LYA_EXP_POLY_SPLIT>(rec, bin, Lt, Rt, order, N, NT, K, tau_s, tid, nt);
+                tiles_by_four<COMP, false, LYA_EXP_POLY_SPLIT>(rec, bin, Lt, Rt, order, ok0, ok1, ext, N, NT, K,
+                                                               tau_s, tid, nt);
         }
         g.sync();
     } else if (warp_tot[kRunTotal] >= kLongRun * NT) {
-        tiles_by_four<COMP, AVG, LYA_EXP_MUFU>(rec, bin, Lt, Rt, order, N, NT, K, tau_s, tid, nt);
+        tiles_by_four<COMP, AVG, LYA_EXP_MUFU>(rec, bin, Lt, Rt, order, ok0, ok1, ext, N, NT, K, tau_s, tid, nt);
         g.sync();
     } else {
     const int lane_q = tid & (kLanesPerTile - 1);
@@ -877,9 +952,13 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
         const int tile = order[i];
         const int o = kTile * tile + 2 * lane_q;
         float S[2] = {0.f, 0.f}, C[2] = {0.f, 0.f};
-        for_tile_run(bin, N, Lt[tile], Rt[tile], [&](int k0, int k1, float shift) {
-            pair2_segment<COMP, AVG>(rec, k0, k1, (float)o + shift, S, C);
-        });
+        if (ext) {
+            pair2_segment<COMP, AVG>(rec, ok0[i], ok1[i], (float)o, S, C);
+        } else {
+            for_tile_run(bin, N, Lt[tile], Rt[tile], [&](int k0, int k1, float shift) {
+                pair2_segment<COMP, AVG>(rec, k0, k1, (float)o + shift, S, C);
+            });
+        }
         if (o < N) tau_s[o] = K * (COMP ? __fsub_rn(S[0], C[0]) : S[0]);
         if (o + 1 < N) tau_s[o + 1] = K * (COMP ? __fsub_rn(S[1], C[1]) : S[1]);
     }
