@@ -45,8 +45,8 @@ ALG_BYTES_PER_PX = 16          # rho, vpec, T read (12 B) + tau written (4 B)
 # scaled by the number of skewers, with the SHA-1 of the kernel source each
 # was taken on: reported as null once paper_1105_4747_gb300/csrc/tau_extract.cu
 # differs from it.
-TAU_DRAM_PROFILE = {"gpc": ((402.740480e6 + 75.112192e6) / 8192, "1a6aa4c2d55139081b5e4f0e8a903b56bd3b81c3"),
-                    "grid1536": ((2.416990e9 + 0.744570880e9) / 131072, "1a6aa4c2d55139081b5e4f0e8a903b56bd3b81c3")}
+TAU_DRAM_PROFILE = {"gpc": ((402.759680e6 + 84.048896e6) / 8192, "e94ecb7c49f76d40b27344ab795aa809d7166084"),
+                    "grid1536": ((2.416098e9 + 0.755907328e9) / 131072, "e94ecb7c49f76d40b27344ab795aa809d7166084")}
 
 
 def tau_code_hash() -> str:

@@ -72,6 +72,22 @@ __global__ void __launch_bounds__(kThreads) mf_init_kernel(const float* __restri
     if (s_go) proxy_start(st);
 }
 
+// ---- the root-find state set on the device (no host copy to wait for) -----------
+__global__ void __launch_bounds__(kThreads) mf_state_init_kernel(MFState* st, double Ft, double tol, long long n,
+                                                               int max_iter)
+{
+    unsigned long long* w = reinterpret_cast<unsigned long long*>(st);
+    for (int k = threadIdx.x; k < (int)(sizeof(MFState) / sizeof(unsigned long long)); k += blockDim.x) w[k] = 0ull;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->Ft = Ft;
+        st->tol = tol;
+        st->n = n;
+        st->max_iter = max_iter;
+        st->status = LYA_ENOCONV;
+    }
+}
+
 // ---- one Halley pass: g, g' and g'' in one read of tau -----------------------------
 __global__ void __launch_bounds__(kThreads) mf_newton_kernel(const float* __restrict__ tau, long long n,
                                                            MFState* st, Partial* part)
@@ -296,7 +312,7 @@ __global__ void __launch_bounds__(kThreads) field_check_kernel(const float* __re
 int grid_for(long long n)
 {
     const long long want = (n + kThreads - 1) / kThreads;
-    const long long cap = 8LL * sm_count();
+    const long long cap = 4LL * sm_count();
     return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
@@ -353,16 +369,15 @@ static lya_status solve_on_scratch(const float* tau, int64_t n, double target, d
                                    lya_flux_stats_t* stats_out = nullptr)
 {
     static_assert(sizeof(MFState) % 8 == 0, "state layout");
-    MFState hs{};                                   // host copy (no heap allocation)
+    MFState hs{};                                   // host copy of the state's header (no heap allocation)
     MFState* h = &hs;
-    h->Ft = target;
-    h->tol = tol;
-    h->n = n;
-    h->max_iter = max_iter;
-    h->status = LYA_ENOCONV;
+    StatsOut hs2{};
     lya_status result = LYA_ENOCONV;
-    cudaError_t err = cudaMemcpyAsync(st, h, sizeof(MFState), cudaMemcpyHostToDevice, stream);
-    if (err == cudaSuccess) err = cudaStreamSynchronize(stream);   // h is reused below
+    // the state is set by a kernel, so nothing waits for the optical-depth
+    // kernel ahead of it on the stream
+    mf_state_init_kernel<<<1, kThreads, 0, stream>>>(st, target, tol, (long long)n, max_iter);
+    count_launch();
+    cudaError_t err = cudaGetLastError();
     if (err == cudaSuccess) {
         mf_init_kernel<<<grid, kThreads, 0, stream>>>(tau, n, st, part);
         count_launch();
@@ -382,6 +397,9 @@ static lya_status solve_on_scratch(const float* tau, int64_t n, double target, d
         count_launch();
         err = cudaGetLastError();
         if (err == cudaSuccess) err = cudaMemcpyAsync(h, st, offsetof(MFState, hist), cudaMemcpyDeviceToHost, stream);
+        // the statistics ride along (kept only once the state says done), one wait for both
+        if (err == cudaSuccess && stats_out)
+            err = cudaMemcpyAsync(&hs2, sout, sizeof(StatsOut), cudaMemcpyDeviceToHost, stream);
         if (err == cudaSuccess) err = cudaStreamSynchronize(stream);
         if (err != cudaSuccess) break;
         if (h->done) {
@@ -395,18 +413,13 @@ static lya_status solve_on_scratch(const float* tau, int64_t n, double target, d
     }
     if (err == cudaSuccess && result == LYA_OK) *A_out = h->A;
     if (err == cudaSuccess && result == LYA_OK && stats_out) {
-        StatsOut hs2{};
-        err = cudaMemcpyAsync(&hs2, sout, sizeof(StatsOut), cudaMemcpyDeviceToHost, stream);
-        if (err == cudaSuccess) err = cudaStreamSynchronize(stream);
-        if (err == cudaSuccess) {
-            const double nn = (double)n;
-            const double m1 = hs2.m1 / nn, m2 = hs2.m2 / nn;
-            stats_out->mean_flux = 0.5 + m1;
-            stats_out->var_flux = m2 - m1 * m1;
-            stats_out->tau_eff = -log(stats_out->mean_flux);
-            for (int k = 0; k < 21; ++k) stats_out->pdf[k] = (int64_t)hs2.pdf[k];
-            stats_out->n = n;
-        }
+        const double nn = (double)n;
+        const double m1 = hs2.m1 / nn, m2 = hs2.m2 / nn;
+        stats_out->mean_flux = 0.5 + m1;
+        stats_out->var_flux = m2 - m1 * m1;
+        stats_out->tau_eff = -log(stats_out->mean_flux);
+        for (int k = 0; k < 21; ++k) stats_out->pdf[k] = (int64_t)hs2.pdf[k];
+        stats_out->n = n;
     }
     if (err != cudaSuccess) return err == cudaErrorMemoryAllocation ? LYA_ENOMEM : LYA_ECUDA;
     return result;

@@ -18,7 +18,7 @@ constexpr double kLog2e = 1.4426950408889634;
 constexpr float kLn2f = 0.69314718055994531f;
 
 // Streams x[0..n) through f(index, value), thread tid of nthr.  When x is
-// 16-byte aligned each thread keeps four float4 loads in flight per step (the
+// 16-byte aligned each thread keeps eight float4 loads in flight per step (the
 // bytes in flight, not the instruction count, bound these HBM passes); the
 // last n % 4 values and unaligned inputs take the scalar path.
 template <typename Fn>
@@ -29,12 +29,12 @@ __device__ __forceinline__ void stream_f32(const float* __restrict__ x, long lon
         const float4* __restrict__ x4 = reinterpret_cast<const float4*>(x);
         const long long n4 = n >> 2;
         long long i = tid;
-        for (; i + 3 * nthr < n4; i += 4 * nthr) {
-            float4 v[4];
+        for (; i + 7 * nthr < n4; i += 8 * nthr) {
+            float4 v[8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) v[u] = x4[i + u * nthr];
+            for (int u = 0; u < 8; ++u) v[u] = x4[i + u * nthr];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < 8; ++u) {
                 const long long b = 4 * (i + u * nthr);
                 f(b, v[u].x); f(b + 1, v[u].y); f(b + 2, v[u].z); f(b + 3, v[u].w);
             }
