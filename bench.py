@@ -45,8 +45,8 @@ ALG_BYTES_PER_PX = 16          # rho, vpec, T read (12 B) + tau written (4 B)
 # scaled by the number of skewers, with the SHA-1 of the kernel source each
 # was taken on: reported as null once paper_1105_4747_gb300/csrc/tau_extract.cu
 # differs from it.
-TAU_DRAM_PROFILE = {"gpc": ((402.759680e6 + 84.048896e6) / 8192, "e94ecb7c49f76d40b27344ab795aa809d7166084"),
-                    "grid1536": ((2.416098e9 + 0.755907328e9) / 131072, "e94ecb7c49f76d40b27344ab795aa809d7166084")}
+TAU_DRAM_PROFILE = {"gpc": ((402.752000e6 + 83.244288e6) / 8192, "750906521fa3b777fea8f0c41842111b8569758a"),
+                    "grid1536": ((2.416163e9 + 0.755671552e9) / 131072, "750906521fa3b777fea8f0c41842111b8569758a")}
 
 
 def tau_code_hash() -> str:

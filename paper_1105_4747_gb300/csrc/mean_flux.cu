@@ -141,11 +141,10 @@ __global__ void __launch_bounds__(kThreads) mf_flux_kernel(const float* __restri
     split_rate(st->A, a_hi, a_lo);
     KahanF32 s0, m1, m2;
     float s0c = 0.f;
-    stream_f32(tau, n, [&](long long i, float t) {
+    auto proc = [&](float t) {
         float e, c;
         exp_neg(t, a_hi, a_lo, e, c);
         const float f = e + c;
-        if (F) F[i] = f;
         s0.add(e);
         s0c += c;
         if constexpr (STATS) {
@@ -154,7 +153,49 @@ __global__ void __launch_bounds__(kThreads) mf_flux_kernel(const float* __restri
             m2.add(d * d);
             mine[pdf_bin(f)] += 1u;
         }
-    });
+        return f;
+    };
+    // the values in the order stream_f32 gives them, F written back as float4
+    // where tau and F are 16-byte aligned
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x, nthr = (long long)gridDim.x * blockDim.x;
+    if ((reinterpret_cast<uintptr_t>(tau) & 15) == 0 && (!F || (reinterpret_cast<uintptr_t>(F) & 15) == 0)) {
+        const float4* __restrict__ t4 = reinterpret_cast<const float4*>(tau);
+        float4* __restrict__ F4 = reinterpret_cast<float4*>(F);
+        const long long n4 = n >> 2;
+        long long i = tid;
+        for (; i + 7 * nthr < n4; i += 8 * nthr) {
+            float4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = t4[i + u * nthr];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                float4 o;
+                o.x = proc(v[u].x);
+                o.y = proc(v[u].y);
+                o.z = proc(v[u].z);
+                o.w = proc(v[u].w);
+                if (F) F4[i + u * nthr] = o;
+            }
+        }
+        for (; i < n4; i += nthr) {
+            const float4 v = t4[i];
+            float4 o;
+            o.x = proc(v.x);
+            o.y = proc(v.y);
+            o.z = proc(v.z);
+            o.w = proc(v.w);
+            if (F) F4[i] = o;
+        }
+        for (long long k = 4 * n4 + tid; k < n; k += nthr) {
+            const float f = proc(tau[k]);
+            if (F) F[k] = f;
+        }
+    } else {
+        for (long long k = tid; k < n; k += nthr) {
+            const float f = proc(tau[k]);
+            if (F) F[k] = f;
+        }
+    }
     constexpr int K = STATS ? 4 : 2;
     __shared__ double sh[K][32];
     double v[K];

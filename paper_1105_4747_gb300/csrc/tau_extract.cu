@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <cfloat>
 #include <cstdint>
+#include <mutex>
 
 #include "lya_device.cuh"
 #include "lya_internal.h"
@@ -1096,26 +1097,67 @@ size_t tau_smem_bytes(int n_pix, int w_max, int precision)
     return tile_smem_bytes(n_pix, w_max);
 }
 
+// Per kernel and device: the dynamic shared memory it has been allowed, and
+// the resident CTAs of the device for the last (threads, shared memory) asked
+// for, so that repeated launches skip the attribute and occupancy queries.
+struct LaunchInfo {
+    const void* fn;
+    int dev;
+    size_t smem_allowed;
+    int nt;
+    size_t smem;
+    int64_t resident;
+};
+static std::mutex g_launch_mu;
+static LaunchInfo g_launch_info[64];
+static int g_launch_n = 0;
+
 template <typename K>
 static cudaError_t launch_kernel(K kernel, const TauLaunch& L0, size_t smem, int nt, cudaStream_t stream,
                                  bool prefetch = false)
 {
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    const void* fn = reinterpret_cast<const void*>(kernel);
+    int64_t resident = -1;
+    {
+        std::lock_guard<std::mutex> lk(g_launch_mu);
+        LaunchInfo* li = nullptr;
+        for (int i = 0; i < g_launch_n; ++i)
+            if (g_launch_info[i].fn == fn && g_launch_info[i].dev == dev) li = &g_launch_info[i];
+        if (!li || li->smem_allowed < smem) {
+            e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+            if (e != cudaSuccess) return e;
+            if (!li && g_launch_n < 64) {
+                li = &g_launch_info[g_launch_n++];
+                *li = LaunchInfo{fn, dev, 0, 0, 0, -1};
+            }
+            if (li) li->smem_allowed = smem;
+        }
+        if (prefetch) {
+            // one wave ahead: the CTAs resident on the whole device at once
+            if (li && li->nt == nt && li->smem == smem && li->resident >= 0) {
+                resident = li->resident;
+            } else {
+                int sms = 0, per_sm = 0;
+                if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, nt, smem) == cudaSuccess)
+                    resident = (int64_t)sms * per_sm;
+                (void)cudaGetLastError();
+                if (li && resident >= 0) {
+                    li->nt = nt;
+                    li->smem = smem;
+                    li->resident = resident;
+                }
+            }
+        }
+    }
     if (L0.n_rows == 0) return cudaSuccess;
     TauLaunch L = L0;
-    L.pf_ahead = 0;
-    if (prefetch) {
-        // one wave ahead: the CTAs resident on the whole device at once
-        int dev = 0, sms = 0, per_sm = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, nt, smem) == cudaSuccess)
-            L.pf_ahead = (int64_t)sms * per_sm;
-        (void)cudaGetLastError();
-    }
+    L.pf_ahead = resident > 0 ? resident : 0;
     kernel<<<(unsigned)L.n_rows, nt, smem, stream>>>(L);
     count_launch();
     return cudaGetLastError();
