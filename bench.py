@@ -49,6 +49,30 @@ TAU_DRAM_PROFILE = {"gpc": ((402.752000e6 + 83.244288e6) / 8192, "750906521fa3b7
                     "grid1536": ((2.416163e9 + 0.755671552e9) / 131072, "750906521fa3b777fea8f0c41842111b8569758a")}
 
 
+# ncu pipe utilisation of the same tau-kernel launch as TAU_DRAM_PROFILE["gpc"]
+# (8,192 skewers, --set full, profiles/tau_tile_kernel_gpc_8192x4096.md), with
+# the code hash it was taken on: reported as null once the kernel differs.
+TAU_PIPE_PROFILE = {"gpc": ({"fma_pct": 21.9, "xu_pct": 20.7, "alu_pct": 40.7, "lsu_pct": 18.8,
+                             "issue_active_pct": 65.1}, "750906521fa3b777fea8f0c41842111b8569758a")}
+FP32_OPS_PER_PAIR = 6          # per pair of the sum: argument (2), square, exponent scale, weight, add
+KB_J_PER_K = 1.380649e-23
+M_H_KG = 1.6735575e-27
+
+
+def algorithmic_pairs_per_px(rho, v, t, du, window=8.0):
+    """Pairs (i, j) of the Eq. 6 sum within the window: |i du - (j du + v_j)| <= window b_j,
+    b_j = (2 k T_j / m_H)^(1/2), counted exactly on host rows (sources with rho > 0),
+    per output pixel."""
+    rho = np.asarray(rho, dtype=np.float64)
+    N = rho.shape[1]
+    u = np.arange(N)[None, :] * du + np.asarray(v, dtype=np.float64)
+    b = np.sqrt(2.0 * KB_J_PER_K * np.asarray(t, dtype=np.float64) / M_H_KG) / 1e3
+    lo = np.ceil((u - window * b) / du)
+    hi = np.floor((u + window * b) / du)
+    cnt = np.clip(hi - lo + 1.0, 0.0, float(N))
+    return float(cnt[rho > 0].sum() / rho.size)
+
+
 def tau_code_hash() -> str:
     """SHA-1 of the optical-depth kernel's code: tau_extract.cu and the headers
     it includes, with comments and blank lines removed (a comment edit does not
@@ -605,6 +629,14 @@ def run_ours(args):
     # device fields and two F buffers let step k+1's inputs cross to the device
     # (a loader thread, lya_field_load on its own stream) and step k-1's F
     # cross back (a copy stream) while step k computes.
+    # algorithmic pairs of the sum per pixel, counted on 64 rows of the workload
+    if grid:
+        r64, v64, t64 = ls.grid_rows(spec, np.arange(64))
+    else:
+        r64, v64, t64 = rho[:64], v[:64], t[:64]
+    pairs_px = algorithmic_pairs_per_px(r64, v64, t64, lya.field_pixel_width(field))
+    del r64, v64, t64
+
     e2e = None
     if not args.no_e2e and not grid:
         e2e = run_e2e(lya, torch, field, spec, S, params, target, rho, v, t, tau, F,
@@ -623,6 +655,20 @@ def run_ours(args):
                 "peak_source": "measured" if peaks else "fallback",
                 "alg_bytes_per_launch": ALG_BYTES_PER_PX * n_px}
 
+    # the pair sum's arithmetic against the FP32 and MUFU (XU) pipe peaks at the
+    # maximum SM clock: algorithmic pairs x FP32 operations per pair, one ex2 each
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    clk_hz = (peaks["sm_max_mhz"] if peaks else 2070.0) * 1e6
+    pairs = pairs_px * n_px
+    pipe_ncu, pipe_hash = TAU_PIPE_PROFILE.get(args.workload, (None, None))
+    pipes = {"alg_pairs_per_px": pairs_px, "fp32_ops_per_pair": FP32_OPS_PER_PAIR,
+             "fp32_achieved": pairs * FP32_OPS_PER_PAIR / (tau_ms / 1e3), "fp32_peak": sms * 128 * clk_hz,
+             "fp32_frac": pairs * FP32_OPS_PER_PAIR / (tau_ms / 1e3) / (sms * 128 * clk_hz),
+             "xu_achieved": pairs / (tau_ms / 1e3), "xu_peak": sms * 16 * clk_hz,
+             "xu_frac": pairs / (tau_ms / 1e3) / (sms * 16 * clk_hz),
+             "unit": "operations/s", "peak_clock_mhz": clk_hz / 1e6, "sms": sms,
+             "ncu_pipe_pct": pipe_ncu if pipe_ncu and tau_code_hash() == pipe_hash else None}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not grid:
         cpu = oracle_timing(spec, args.cpu_seconds)
@@ -640,7 +686,7 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": workload_config(spec, S, {"parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                                                     "A": A, "mean_flux": st.mean_flux}, grid),
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "roofline": roofline, "pipes": pipes, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "serving": serving, "post": post}
         print(json.dumps(line), flush=True)
     field.close()
