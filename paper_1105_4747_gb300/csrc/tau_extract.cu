@@ -302,6 +302,7 @@ constexpr int kTileKeys = 256;                   // tile-order histogram (counts
 constexpr int kReachLow = -(1 << 28);
 constexpr int kReachHigh = 1 << 28;
 constexpr int kEmptyRun = 30000;                 // L of a tile no source reaches (L > R)
+constexpr int kWrapTile = 8192;                  // tile-order flag: the run spans more than the skewer (NT <= 1024)
 constexpr float kSqrtLn2 = 0.83255461115769775f;
 constexpr float kHalfSqrtPi = 0.88622692545275801f;
 
@@ -644,21 +645,48 @@ __device__ __forceinline__ void pair4_segment(const float4* __restrict__ rec, in
     }
 }
 
+// A tile whose candidate run would span more than the whole skewer (boxes so
+// small that a line's window reaches past half the box): every source once,
+// records [k0, k1) with targets in [0, N), at the periodic image nearest each
+// pixel (velocity difference in [-V/2, V/2), as Eq. 6 is read), NPX pixels
+// fo .. fo + NPX - 1.  Slow, and met only in such boxes.
+template <bool COMP, bool AVG, int NPX>
+__device__ __forceinline__ void wrap_segment(const float4* __restrict__ rec, int k0, int k1, float fo, float Nf,
+                                          float (&S)[NPX], float (&C)[NPX])
+{
+    for (int k = k0; k < k1; ++k) {
+        const float4 r = rec[k];                                    // r = {a, c r, w, t}
+#pragma unroll
+        for (int m = 0; m < NPX; ++m) {
+            const float mi = (fo + (float)m) - r.w;                  // exact: integers
+            float x = fmaf(mi, r.x, -r.y);
+            if (x >= 0.5f * Nf * r.x) x = fmaf(mi - Nf, r.x, -r.y);
+            else if (x < -0.5f * Nf * r.x) x = fmaf(mi + Nf, r.x, -r.y);
+            const float t = AVG ? r.z * cell_erf(x, 0.5f * r.x) : r.z * ex2(-(x * x));
+            if constexpr (COMP) kahan_fold(S[m], C[m], t);
+            else S[m] += t;
+        }
+    }
+}
+
 // Step 7 with two lanes per tile, four pixels each, over the tiles in order.
 template <bool COMP, bool AVG, int EXP>
 __device__ __forceinline__ void tiles_by_four(const float4* __restrict__ rec, const int* bin, const short* Lt,
                                               const short* Rt, const short* order, const short* ok0,
                                               const short* ok1, bool ext, int N, int NT, float K,
-                                              float* tau_s, int tid, int nt)
+                                              float* tau_s, int tid, int nt, int base, int nsrc)
 {
     const int half = tid & 1, ng = nt / 2, grp = tid / 2;
     for (int round = 0; round * ng < NT; ++round) {
         const int i = round * ng + ((round & 1) ? ng - 1 - grp : grp);
         if (i >= NT) continue;
-        const int tile = order[i];
+        const int ot = order[i];
+        const int tile = ot & (kWrapTile - 1);
         const int o = kTile * tile + 4 * half;
         float S[4] = {0.f, 0.f, 0.f, 0.f}, C[4] = {0.f, 0.f, 0.f, 0.f};
-        if (ext) {
+        if (ot & kWrapTile) {
+            wrap_segment<COMP, AVG, 4>(rec, base, base + nsrc, (float)o, (float)N, S, C);
+        } else if (ext) {
             pair4_segment<COMP, AVG, EXP>(rec, ok0[i], ok1[i], (float)o, S, C);
         } else {
             for_tile_run(bin, N, Lt[tile], Rt[tile], [&](int k0, int k1, float shift) {
@@ -849,6 +877,7 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
     // 6. tiles ordered by candidate count, largest first (counting sort)
     constexpr int kMaxTilesPerThread = (MAXQ + kTile - 1) / kTile;   // NT <= MAXQ nt / kTile
     int tkey[kMaxTilesPerThread], kk0[kMaxTilesPerThread], kk1[kMaxTilesPerThread];
+    bool wrap[kMaxTilesPerThread];
     int runs = 0;
 #pragma unroll
     for (int u = 0; u < kMaxTilesPerThread; ++u) {
@@ -872,7 +901,10 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
                 rx = Rt[tile];
             }
             int c = 0;
-            if (ext) {
+            wrap[u] = rx - lx + 1 > N;        // the run would hold a source twice: every source once instead
+            if (wrap[u]) {
+                c = nsrc;
+            } else if (ext) {
                 // the run as one range of the record array with its copies
                 kk0[u] = lx >= 0 ? base + bin[lx] : bin[lx + N] - (nsrc - P);
                 kk1[u] = rx < N ? base + bin[rx + 1] : base + nsrc + bin[rx - N + 1];
@@ -918,8 +950,8 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
     for (int u = 0; u < kMaxTilesPerThread; ++u) {
         if (tkey[u] < 0) continue;
         const int pos = atomicAdd(&tile_hist[tkey[u]], 1);
-        order[pos] = (short)(tid + u * nt);
-        if (ext) {
+        order[pos] = (short)((tid + u * nt) | (wrap[u] ? kWrapTile : 0));
+        if (ext && !wrap[u]) {
             ok0[pos] = (short)kk0[u];
             ok1[pos] = (short)kk1[u];
         }
@@ -935,14 +967,14 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
         if constexpr (ALT_EXP && !AVG) {
             if (L.exp_method == LYA_EXP_RECURRENCE)
                 tiles_by_four<COMP, false, LYA_EXP_RECURRENCE>(rec, bin, Lt, Rt, order, ok0, ok1, ext, N, NT, K,
-                                                               tau_s, tid, nt);
+                                                               tau_s, tid, nt, base, nsrc);
             else
                 tiles_by_four<COMP, false, LYA_EXP_POLY_SPLIT>(rec, bin, Lt, Rt, order, ok0, ok1, ext, N, NT, K,
-                                                               tau_s, tid, nt);
+                                                               tau_s, tid, nt, base, nsrc);
         }
         g.sync();
     } else if (warp_tot[kRunTotal] >= kLongRun * NT) {
-        tiles_by_four<COMP, AVG, LYA_EXP_MUFU>(rec, bin, Lt, Rt, order, ok0, ok1, ext, N, NT, K, tau_s, tid, nt);
+        tiles_by_four<COMP, AVG, LYA_EXP_MUFU>(rec, bin, Lt, Rt, order, ok0, ok1, ext, N, NT, K, tau_s, tid, nt, base, nsrc);
         g.sync();
     } else {
     const int lane_q = tid & (kLanesPerTile - 1);
@@ -950,10 +982,13 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
     for (int round = 0; round * npairs < NT; ++round) {
         const int i = round * npairs + ((round & 1) ? npairs - 1 - pair : pair);
         if (i >= NT) continue;
-        const int tile = order[i];
+        const int ot = order[i];
+        const int tile = ot & (kWrapTile - 1);
         const int o = kTile * tile + 2 * lane_q;
         float S[2] = {0.f, 0.f}, C[2] = {0.f, 0.f};
-        if (ext) {
+        if (ot & kWrapTile) {
+            wrap_segment<COMP, AVG, 2>(rec, base, base + nsrc, (float)o, (float)N, S, C);
+        } else if (ext) {
             pair2_segment<COMP, AVG>(rec, ok0[i], ok1[i], (float)o, S, C);
         } else {
             for_tile_run(bin, N, Lt[tile], Rt[tile], [&](int k0, int k1, float shift) {

@@ -159,6 +159,38 @@ def test_uniform_field_and_single_absorber(lya, orc):
     assert np.ptp(tg[0]) / tg[0].mean() < 1e-6
 
 
+@pytest.mark.parametrize("target", [0, -1])
+def test_sources_crowded_at_the_seam(lya, orc, target):
+    """Every source of a skewer shifted onto one pixel at the periodic seam
+    (pixel 0, or pixel N - 1): more seam records than the kernel reserves
+    copies for, so the tile runs are taken in pieces across the seam."""
+    N = 256
+    spec = ls.TINY_20MPC
+    du = lya.field_pixel_width(make_field(lya, spec, np.ones((1, N), np.float32),
+                                          np.zeros((1, N), np.float32), np.full((1, N), 1.5e4, np.float32)))
+    j = np.arange(N, dtype=np.float64)
+    rng = np.random.default_rng(5)
+    rho = np.stack([np.ones(N), rng.uniform(0.2, 3.0, N)]).astype(np.float32)
+    v = np.stack([(target % N - j) * du, (target % N - j) * du + rng.uniform(-0.4, 0.4, N) * du]).astype(np.float32)
+    t = np.stack([np.full(N, 1.5e4), rng.uniform(8e3, 3e4, N)]).astype(np.float32)
+    field = make_field(lya, spec, rho, v, t)
+    tg = lya.extract_skewers(field, lya.ExtractParams()).cpu().numpy()
+    to = orc.tau(oparams(orc, spec), rho, v, t)
+    assert_tau_close(tg, to, 1.0 / float(to.max()))
+
+
+@pytest.mark.parametrize("n_pix", [18, 258, 1030])
+def test_lengths_not_a_multiple_of_four(lya, orc, n_pix):
+    """Scalar loads and bin searches (rows not 16-byte aligned), against the oracle."""
+    spec = ls.TINY_20MPC.with_(n_pix=n_pix, box=20.0 * n_pix / 256, seed=13)
+    rho, v, t = ls.skewers(spec, np.arange(5))
+    field = make_field(lya, spec, rho, v, t)
+    tg, A_g, F_g, to, A_o, F_o = end_to_end(lya, orc, field, lya.ExtractParams(), oparams(orc, spec),
+                                             rho, v, t, ls.TINY_20MPC_FT)
+    assert_tau_close(tg, to, A_o)
+    assert float(np.abs(F_g - F_o).max()) <= F_ATOL
+
+
 def test_ids_subset_duplicates_and_errors(lya):
     import torch
     spec = ls.TINY_20MPC
