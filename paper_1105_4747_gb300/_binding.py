@@ -16,7 +16,9 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_HERE, "_build", "liblya.so")
+# LYA_LIBRARY may name another build of the same library (the bounds-checked
+# one, build(checked=True)); there is no other implementation to fall back to
+_LIB_PATH = os.environ.get("LYA_LIBRARY") or os.path.join(_HERE, "_build", "liblya.so")
 _lock = threading.Lock()
 _lib = None
 

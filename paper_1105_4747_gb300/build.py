@@ -42,11 +42,23 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile and link liblya.so; returns its path."""
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), checked: bool = False) -> str:
+    """Compile and link liblya.so; returns its path.
+
+    checked: a separate build (``_build_checked/liblya.so``) with -DLYA_CHECKED,
+    whose optical-depth kernels check every shared-memory index of the tile
+    gather and record a failure in the launch's error word."""
+    if checked:
+        return _build_into(os.path.join(HERE, "_build_checked"), force, verbose,
+                           list(extra_flags) + ["-DLYA_CHECKED"])
+    return _build_into(BUILD, force, verbose, list(extra_flags))
+
+
+def _build_into(build_dir: str, force: bool, verbose: bool, extra_flags) -> str:
+    lib = os.path.join(build_dir, "liblya.so")
+    if not force and os.path.exists(lib) and all(os.path.getmtime(p) <= os.path.getmtime(lib) for p in _deps()):
+        return lib
+    os.makedirs(build_dir, exist_ok=True)
     cc = nvcc()
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                     "-I", os.path.join(ROOT, "include"), "-I", CSRC] + list(extra_flags)
@@ -54,7 +66,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         flags += ["-Xptxas", "-v"]
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         r = subprocess.run([cc, "-c", src, "-o", obj] + flags, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stderr}")
@@ -65,13 +77,13 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     if verbose:
         for _, log in results:
             print(log)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     r = subprocess.run([cc, "-shared", "-o", tmp] + [o for o, _ in results] + ARCH +
                        ["-Xcompiler", "-fPIC"], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

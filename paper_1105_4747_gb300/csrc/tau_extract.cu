@@ -33,6 +33,20 @@
 #include "lya_internal.h"
 #include "serve_internal.h"
 
+// LYA_CHECKED builds (a stand-in for a memory checker): every shared-memory
+// index of the tile gather is checked before use, and a failed check sets
+// bit 2 (value 4) of the launch's error word instead of trapping.
+#ifdef LYA_CHECKED
+#define LYA_BOUND(cond)                       \
+    do {                                      \
+        if (!(cond)) atomicOr(L.err, 4);      \
+    } while (0)
+#else
+#define LYA_BOUND(cond) \
+    do {                \
+    } while (0)
+#endif
+
 namespace lya {
 namespace {
 
@@ -730,6 +744,8 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
 
     // 1. every input load issued up front (float4 when rows are 16-byte aligned)
     const bool vec = (N & 3) == 0;
+    const int rec_cap = round_up4(N + Cx);                  // records the shared memory holds
+    LYA_BOUND(N <= MAXQ * nt && NT <= kWrapTile);
     float r_[MAXQ], v_[MAXQ], T_[MAXQ];
     if (vec) {
 #pragma unroll
@@ -804,6 +820,7 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
             bb_[q] = s.bb;
             w_[q] = s.w;
             th_[q] = (s.t << 16) | s.h;
+            LYA_BOUND(s.t >= 0 && s.t < N && s.h >= 0 && s.h <= Wd);
             atomicAdd(&cnt[s.t], 1);
             if (local) {
                 atomicMax(&reach[s.t], s.h);
@@ -836,8 +853,10 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
         const int t = th_[q] >> 16, h = th_[q] & 0xffff;
         const int pos = atomicAdd(&cnt[t], 1);
         if (pos >= N) { atomicOr(L.err, 2); th_[q] = -1; continue; }   // input changed under the kernel
+        LYA_BOUND(base + pos >= 0 && base + pos < rec_cap);
         rec[base + pos] = make_float4(a_[q], bb_[q], w_[q], (float)t);
         if (local) continue;
+        LYA_BOUND(t >= 0 && t + Wd < NE);
         atomicMax(&reach[t + Wd], t + h);
         if (t >= N - Wd) atomicMax(&reach[t - N + Wd], t - N + h);
         if (t < Wd) atomicMax(&reach[t + N + Wd], t + N + h);
@@ -890,6 +909,7 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
                 // reaches it, last bin at most hs right of it likewise (bins
                 // past the seam are read at their periodic image)
                 const int lo = kTile * tile, hi = min(lo + kTile - 1, N - 1);
+                LYA_BOUND(hs <= Wd && lo - hs > -N && hi + hs < 2 * N);
                 lx = local_run_left(reach, N, lo, hs, vec);
                 rx = local_run_right(reach, N, hi, hs, vec);
                 if (!ext) {
@@ -906,9 +926,12 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
                 c = nsrc;
             } else if (ext) {
                 // the run as one range of the record array with its copies
+                LYA_BOUND(lx >= -N && lx < N && rx >= 0 && rx < 2 * N);
                 kk0[u] = lx >= 0 ? base + bin[lx] : bin[lx + N] - (nsrc - P);
                 kk1[u] = rx < N ? base + bin[rx + 1] : base + nsrc + bin[rx - N + 1];
                 c = kk1[u] - kk0[u];
+                LYA_BOUND(kk0[u] >= 0 && kk0[u] <= kk1[u] && kk1[u] <= base + nsrc + npost &&
+                          base + nsrc + npost <= rec_cap && kk1[u] < 32768);
             } else {
                 for_tile_run(bin, N, lx, rx, [&](int k0, int k1, float) { c += k1 - k0; });
             }
@@ -921,6 +944,7 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
     if (ext) {
         // the seam copies: bins [N - hs, N) in front as t - N, bins [0, hs) behind as t + N
         for (int e = tid; e < P + npost; e += nt) {
+            LYA_BOUND(base + nsrc + npost <= rec_cap && nsrc - P >= 0);
             if (e < P) {
                 float4 r = rec[base + nsrc - P + e];
                 r.w -= (float)N;
@@ -949,7 +973,9 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
 #pragma unroll
     for (int u = 0; u < kMaxTilesPerThread; ++u) {
         if (tkey[u] < 0) continue;
+        LYA_BOUND(tkey[u] < kTileKeys);
         const int pos = atomicAdd(&tile_hist[tkey[u]], 1);
+        LYA_BOUND(pos >= 0 && pos < NT);
         order[pos] = (short)((tid + u * nt) | (wrap[u] ? kWrapTile : 0));
         if (ext && !wrap[u]) {
             ok0[pos] = (short)kk0[u];
@@ -985,6 +1011,8 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
         const int ot = order[i];
         const int tile = ot & (kWrapTile - 1);
         const int o = kTile * tile + 2 * lane_q;
+        LYA_BOUND(tile < NT && (!ext || (ot & kWrapTile) || (ok0[i] >= 0 && ok0[i] <= ok1[i] && ok1[i] <= rec_cap)));
+        LYA_BOUND(ext || (ot & kWrapTile) || Lt[tile] > Rt[tile] || (Lt[tile] >= -Wd && Rt[tile] < N + Wd));
         float S[2] = {0.f, 0.f}, C[2] = {0.f, 0.f};
         if (ot & kWrapTile) {
             wrap_segment<COMP, AVG, 2>(rec, base, base + nsrc, (float)o, (float)N, S, C);
