@@ -45,15 +45,15 @@ ALG_BYTES_PER_PX = 16          # rho, vpec, T read (12 B) + tau written (4 B)
 # scaled by the number of skewers, with the SHA-1 of the kernel source each
 # was taken on: reported as null once paper_1105_4747_gb300/csrc/tau_extract.cu
 # differs from it.
-TAU_DRAM_PROFILE = {"gpc": ((402.752000e6 + 83.244288e6) / 8192, "750906521fa3b777fea8f0c41842111b8569758a"),
-                    "grid1536": ((2.416163e9 + 0.755671552e9) / 131072, "750906521fa3b777fea8f0c41842111b8569758a")}
+TAU_DRAM_PROFILE = {"gpc": ((402.791168e6 + 84.304640e6) / 8192, "f9a9ca4d5e8577cf2bcf435482946284b9181571"),
+                    "grid1536": ((2.416116e9 + 0.755870720e9) / 131072, "f9a9ca4d5e8577cf2bcf435482946284b9181571")}
 
 
 # ncu pipe utilisation of the same tau-kernel launch as TAU_DRAM_PROFILE["gpc"]
 # (8,192 skewers, --set full, profiles/tau_tile_kernel_gpc_8192x4096.md), with
 # the code hash it was taken on: reported as null once the kernel differs.
-TAU_PIPE_PROFILE = {"gpc": ({"fma_pct": 21.9, "xu_pct": 20.7, "alu_pct": 40.7, "lsu_pct": 18.8,
-                             "issue_active_pct": 65.1}, "750906521fa3b777fea8f0c41842111b8569758a")}
+TAU_PIPE_PROFILE = {"gpc": ({"fma_pct": 21.7, "xu_pct": 20.7, "alu_pct": 42.5, "lsu_pct": 18.6,
+                             "issue_active_pct": 65.2}, "f9a9ca4d5e8577cf2bcf435482946284b9181571")}
 FP32_OPS_PER_PAIR = 6          # per pair of the sum: argument (2), square, exponent scale, weight, add
 KB_J_PER_K = 1.380649e-23
 M_H_KG = 1.6735575e-27
