@@ -288,7 +288,10 @@ __global__ void __launch_bounds__(512) tau_kernel(const TauLaunch L)
 // the sorted records (target t - N) and those of bins [0, hs) behind them
 // (t + N), so that every tile's run, across the seam or not, is one range of
 // the record array, stored beside the tile order (when the copies fit the
-// reserved ext_capacity records; else the run is split at the seam).
+// reserved ext_capacity records; else the run is split at the seam).  A tile
+// whose run would span more than the whole skewer (a box so small that a
+// line's window reaches past half of it) takes every source once instead, at
+// the image nearest each pixel (wrap_segment).
 //
 // Load balance: the tiles are counting-sorted by candidate count, largest
 // first, and handed to the threads in that order (reversed on alternate
