@@ -302,9 +302,9 @@ __global__ void __launch_bounds__(512) tau_kernel(const TauLaunch L)
 // with four pixels each.  tau is gathered in shared memory and written to HBM
 // in order at the end.
 //
-// Accumulation per pixel: the terms of four consecutive candidates (read
-// together) are added plainly, then folded into a Kahan sum (compensated
-// variant); or every term is added plainly (naive variant).
+// Accumulation per pixel: the terms of eight consecutive candidates (four
+// where a lane takes four pixels) are added plainly, then folded into a Kahan
+// sum (compensated variant); or every term is added plainly (naive variant).
 //
 // Shared memory: records (N + ext_capacity rounded up to 4) | bin counts
 // (4 + N rounded up to 4; the leading zero makes bin starts and ends one
@@ -458,7 +458,7 @@ __device__ __forceinline__ float cell_erf(float y, float hw)
 
 // Two adjacent pixels fo, fo + 1 (in the run's frame) against candidates [k0, k1).
 // AVG: records hold the averaged-profile constants {du/b, r/b, w sqrt(pi) b/2du, t}.
-template <bool COMP, bool AVG>
+template <bool COMP, bool AVG, int FOLD = 8>
 __device__ __forceinline__ void pair2_segment(const float4* __restrict__ rec, int k0, int k1, float fo,
                                               float (&S)[2], float (&C)[2])
 {
@@ -476,8 +476,34 @@ __device__ __forceinline__ void pair2_segment(const float4* __restrict__ rec, in
     };
     int k = k0;
     if constexpr (COMP && !AVG) {
-        // blocks of four candidates read together, their terms summed plainly
-        // and the block sums folded into the Kahan sums; the last block may be short
+        // blocks of FOLD (8 or 4) candidates, read four at a time, their terms
+        // summed plainly and the block sums folded into the Kahan sums; then a
+        // block of four, then the last one to three
+        for (; FOLD == 8 && k + 8 <= k1; k += 8) {
+            float Q0, Q1;
+            {
+                const float4 r0 = rec[k], r1 = rec[k + 1], r2 = rec[k + 2], r3 = rec[k + 3];
+                float a0, a1, b0, b1, c0, c1, d0, d1;
+                terms(r0, a0, a1);
+                terms(r1, b0, b1);
+                terms(r2, c0, c1);
+                terms(r3, d0, d1);
+                Q0 = (a0 + b0) + (c0 + d0);
+                Q1 = (a1 + b1) + (c1 + d1);
+            }
+            {
+                const float4 r0 = rec[k + 4], r1 = rec[k + 5], r2 = rec[k + 6], r3 = rec[k + 7];
+                float a0, a1, b0, b1, c0, c1, d0, d1;
+                terms(r0, a0, a1);
+                terms(r1, b0, b1);
+                terms(r2, c0, c1);
+                terms(r3, d0, d1);
+                Q0 += (a0 + b0) + (c0 + d0);
+                Q1 += (a1 + b1) + (c1 + d1);
+            }
+            kahan_fold(S[0], C[0], Q0);
+            kahan_fold(S[1], C[1], Q1);
+        }
         for (; k + 4 <= k1; k += 4) {
             const float4 r0 = rec[k], r1 = rec[k + 1], r2 = rec[k + 2], r3 = rec[k + 3];
             float a0, a1, b0, b1, c0, c1, d0, d1;
@@ -721,7 +747,9 @@ __device__ __forceinline__ void tiles_by_four(const float4* __restrict__ rec, co
 // holds the group's tile_smem_bytes(N, w_max) bytes (16-byte aligned);
 // warp_tot (kGroupScanInts ints) and tile_hist (kTileKeys ints, 16-byte aligned) are the
 // group's own shared scratch.  N <= MAXQ * g.nt.
-template <bool COMP, int MAXQ, bool AVG = false, bool ALT_EXP = false>
+// FOLD: candidates per Kahan fold in the two-pixel loop (8, or 4 where registers
+// are scarcer: the serving kernel and the four-sources-per-thread tile kernel).
+template <bool COMP, int MAXQ, bool AVG = false, bool ALT_EXP = false, int FOLD = 8>
 __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __restrict__ rho,
                                             const float* __restrict__ vpec, const float* __restrict__ temp,
                                             float* out, unsigned char* smem, int* warp_tot, int* tile_hist,
@@ -1020,10 +1048,10 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
         if (ot & kWrapTile) {
             wrap_segment<COMP, AVG, 2>(rec, base, base + nsrc, (float)o, (float)N, S, C);
         } else if (ext) {
-            pair2_segment<COMP, AVG>(rec, ok0[i], ok1[i], (float)o, S, C);
+            pair2_segment<COMP, AVG, FOLD>(rec, ok0[i], ok1[i], (float)o, S, C);
         } else {
             for_tile_run(bin, N, Lt[tile], Rt[tile], [&](int k0, int k1, float shift) {
-                pair2_segment<COMP, AVG>(rec, k0, k1, (float)o + shift, S, C);
+                pair2_segment<COMP, AVG, FOLD>(rec, k0, k1, (float)o + shift, S, C);
             });
         }
         if (o < N) tau_s[o] = K * (COMP ? __fsub_rn(S[0], C[0]) : S[0]);
@@ -1069,7 +1097,7 @@ __global__ void __launch_bounds__(NTB, NTB >= 1024 ? 1 : 2) tau_tile_kernel(cons
                 if (q && (reinterpret_cast<uintptr_t>(q) & 15) == 0) prefetch_l2(q, bytes);
         }
     }
-    tile_skewer<COMP, MAXQ, AVG, true>(L, L.rho + sk * (int64_t)N, L.vpec + sk * (int64_t)N,
+    tile_skewer<COMP, MAXQ, AVG, true, (MAXQ >= 8 ? 8 : 4)>(L, L.rho + sk * (int64_t)N, L.vpec + sk * (int64_t)N,
                             L.temp ? L.temp + sk * (int64_t)N : nullptr, out, smem_raw, warp_tot, tile_hist,
                             whole_block());
 }
@@ -1133,7 +1161,8 @@ __global__ void __launch_bounds__(serve::kTauThreads, 1) tau_serve_kernel(unsign
                 const float* rho = Ls.rho + src * (int64_t)N;
                 const float* vpec = Ls.vpec + src * (int64_t)N;
                 const float* temp = Ls.temp ? Ls.temp + src * (int64_t)N : nullptr;
-                tile_skewer<true, serve::kTauMaxQ>(Ls, rho, vpec, temp, out, base, warp_tot, tile_hist, g);
+                tile_skewer<true, serve::kTauMaxQ, false, false, 4>(Ls, rho, vpec, temp, out, base, warp_tot,
+                                                                    tile_hist, g);
             }
         }
         __syncthreads();
