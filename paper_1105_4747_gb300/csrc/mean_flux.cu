@@ -46,13 +46,57 @@ __global__ void __launch_bounds__(kThreads) mf_init_kernel(const float* __restri
     long long smask = 0;
     while ((n >> 22) > smask) smask = 2 * smask + 1;        // sample stride - 1 (a power of 2 minus 1)
     KahanF32 s;
-    long long z = 0, bad = 0;
-    stream_f32(tau, n, [&](long long i, float t) {
-        if (!(t >= 0.f) || !isfinite(t)) { ++bad; return; }
+    unsigned int z = 0, bad = 0;                            // per thread: far below 2^32 values
+    auto take = [&](float t) {
+        if (!(t >= 0.f) || !isfinite(t)) {
+            ++bad;
+            return;
+        }
         s.add(t);
         z += (t == 0.f);
-        if ((i & smask) == 0) atomicAdd(&h_s[t == 0.f ? kHistBins : hist_bin(t)], 1u);
-    });
+    };
+    auto sample = [&](float t) {
+        if (t >= 0.f && isfinite(t)) atomicAdd(&h_s[t == 0.f ? kHistBins : hist_bin(t)], 1u);
+    };
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x, nthr = (long long)gridDim.x * blockDim.x;
+    if (smask >= 3 && (reinterpret_cast<uintptr_t>(tau) & 15) == 0) {
+        // a stride of at least four: only the first value of a float4 whose
+        // index is a multiple of the stride is sampled (same values, same
+        // order as the general loop below)
+        const float4* __restrict__ t4 = reinterpret_cast<const float4*>(tau);
+        const long long n4 = n >> 2;
+        long long i = tid;
+        for (; i + 7 * nthr < n4; i += 8 * nthr) {
+            float4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = t4[i + u * nthr];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                take(v[u].x);
+                take(v[u].y);
+                take(v[u].z);
+                take(v[u].w);
+                if (((4 * (i + u * nthr)) & smask) == 0) sample(v[u].x);
+            }
+        }
+        for (; i < n4; i += nthr) {
+            const float4 v = t4[i];
+            take(v.x);
+            take(v.y);
+            take(v.z);
+            take(v.w);
+            if (((4 * i) & smask) == 0) sample(v.x);
+        }
+        for (long long k = 4 * n4 + tid; k < n; k += nthr) {
+            take(tau[k]);
+            if ((k & smask) == 0) sample(tau[k]);
+        }
+    } else {
+        stream_f32(tau, n, [&](long long i, float t) {
+            take(t);
+            if ((i & smask) == 0) sample(t);
+        });
+    }
     __shared__ double sh[3][32];
     double v[3] = {(double)s.value(), (double)z, (double)bad};
     block_sum<3>(v, sh);
