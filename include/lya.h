@@ -148,8 +148,9 @@ lya_status lya_destroy_field(lya_field field);
 
 /*
  * Read and clear the field's device error word (set by lya_extract_skewers
- * when a skewer id is out of range).  Synchronises the stream; returns
- * LYA_EINVAL if an extraction since the last call saw a bad id.
+ * when a skewer id is out of range; in a library built with -DLYA_CHECKED
+ * also when a bounds check of the optical-depth kernel fails).  Synchronises
+ * the stream; returns LYA_EINVAL if an extraction since the last call set it.
  */
 lya_status lya_field_status(lya_field field, void* stream);
 
@@ -161,8 +162,9 @@ lya_status lya_field_shape(lya_field field, int64_t* n_skewers, int64_t* n_pix);
  * skewer_ids[r], r < n_ids (a DEVICE array of int64 in [0, n_skewers); NULL
  * means all skewers in order, with n_ids == n_skewers).  tau_out is a device
  * array of n_ids * n_pix floats, owned by the caller.  The sum is periodic
- * over the skewer and keeps every pair with |v_H(i) - u(j)| <= nsigma b(j)
- * (a superset of them is allowed).  Out-of-range ids are not checked on the
+ * over the skewer (each source at the image nearest each pixel) and keeps
+ * every pair with |v_H(i) - u(j)| <= nsigma b(j) (a superset of them is
+ * allowed).  Out-of-range ids are not checked on the
  * host; the kernel writes zeros for them and returns LYA_EINVAL at the next
  * synchronising call on the field.
  */

@@ -42,7 +42,8 @@ struct TauLaunch {
     int64_t pf_ahead;         // tile kernel: CTA r prefetches row r + pf_ahead into L2 (0: none)
     int n_pix;
     float* tau_out;           // [n_rows][n_pix]
-    int* err;                 // device error word: bit 0 = skewer id out of range
+    int* err;                 // device error word: bit 0 = skewer id out of range, bit 1 = input
+                              // changed under the kernel, bit 2 = failed bounds check (LYA_CHECKED)
     int w_max;                // bound on every source's window half-width, pixels (<= (n_pix-1)/2)
 
     int t_mode;               // 0 stored T, 1 power law (Eq. 5)
