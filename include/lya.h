@@ -190,21 +190,22 @@ lya_status lya_rescale_mean_flux(const float* tau, int64_t n, double target,
 /*
  * lya_rescale_mean_flux without any device allocation.  The paper has no
  * counterpart: this is a deployment variant for callers that cannot call
- * cudaMalloc (code running inside a CUDA-graph capture they do not own the
- * memory pool of, plug-ins whose host forbids allocation after start-up, or
- * a service whose memory budget is already handed out).  Arguments, results
- * and errors are those of lya_rescale_mean_flux.
+ * cudaMalloc: plug-ins whose host application forbids allocation after
+ * start-up, or a service whose device-memory budget is already handed out.
+ * Arguments, results and errors are those of lya_rescale_mean_flux.
  *
- * Its scratch (the Newton state and one partial sum per CTA) is a fixed
+ * Its scratch (the root-find state and one partial sum per CTA) is a fixed
  * 64 KiB device array inside the library, present on every GPU that loads
  * it until the process exits; the reduction therefore uses at most 1024
  * CTAs, which still covers any n.  The first call on a device looks up the
- * array's device address (once per device, with that device current); make
- * that first call before any stream capture.  Every call rewrites the state
- * it uses, so no clearing is needed between calls, but all calls share the
- * one array: calls whose work overlaps on the GPU (other streams, other host
- * threads on the same device) race and must be serialised by the caller.
- * Synchronises the stream.
+ * array's device address (once per device, with that device current).  At
+ * the start of every call a kernel zeroes and sets the whole state, and every
+ * CTA writes its partial before the last CTA reads them, so nothing carries
+ * over from an earlier call; but all calls share the one array: calls whose
+ * work overlaps on the GPU (other streams, other host threads on the same
+ * device) race and must be serialised by the caller.  The call reads the
+ * state back and synchronises the stream after every round of passes, so the
+ * stream must not be capturing a CUDA graph.
  */
 lya_status lya_rescale_mean_flux_noalloc(const float* tau, int64_t n, double target,
                                          double tol, int max_iter, double* A_out,

@@ -176,6 +176,22 @@ def _stream_handle(stream) -> int:
     return int(s.cuda_stream)
 
 
+def _check_out_like(ref, out, name, ref_name="tau"):
+    """``out`` must hold exactly as many values as ``ref``, on the same device
+    (the kernels write ref.numel() values into it)."""
+    if out.numel() != ref.numel():
+        raise ValueError(f"{name} must have {ref.numel()} elements like {ref_name}, not {out.numel()}")
+    if out.device != ref.device:
+        raise ValueError(f"{name} is on {out.device} but {ref_name} is on {ref.device}")
+    return out
+
+
+def _on(t):
+    """The CUDA device of tensor ``t`` made current for the library call (the
+    C ABI works on the current device)."""
+    return _torch().cuda.device(t.device)
+
+
 def _require_cuda_f32(t, name):
     torch = _torch()
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
@@ -228,6 +244,8 @@ class Field:
                                     _stream_handle(stream) if torch.cuda.is_available() else None,
                                     ctypes.byref(out)), "lya_create_field")
         self._handle = out
+        # the device the field lives on (the current one at creation)
+        self.device = torch.device("cuda", torch.cuda.current_device())
         self.n_skewers, self.n_pix = S, N
         self.has_temp = temp is not None
         self.box, self.z = box, z
@@ -299,18 +317,21 @@ def extract_skewers(field: Field, params: ExtractParams, ids=None, out=None, str
     if ids is None:
         n_ids, ids_ptr = field.n_skewers, None
     else:
-        ids_t = torch.as_tensor(ids, dtype=torch.int64).to("cuda").contiguous()
+        ids_t = torch.as_tensor(ids, dtype=torch.int64).to(field.device).contiguous()
         n_ids, ids_ptr = ids_t.numel(), ids_t.data_ptr()
     if out is None:
-        out = torch.empty((n_ids, field.n_pix), dtype=torch.float32, device="cuda")
+        out = torch.empty((n_ids, field.n_pix), dtype=torch.float32, device=field.device)
     else:
         _require_cuda_f32(out, "out")
         if out.numel() != n_ids * field.n_pix:
             raise ValueError("out has the wrong size")
+        if out.device != field.device:
+            raise ValueError(f"out is on {out.device} but the field is on {field.device}")
     p = params._c()
-    _check(lib.lya_extract_skewers(field.handle, ctypes.byref(p), ids_ptr, n_ids,
-                                   out.data_ptr() if n_ids else None, _stream_handle(stream)),
-           "lya_extract_skewers")
+    with torch.cuda.device(field.device):
+        _check(lib.lya_extract_skewers(field.handle, ctypes.byref(p), ids_ptr, n_ids,
+                                       out.data_ptr() if n_ids else None, _stream_handle(stream)),
+               "lya_extract_skewers")
     if ids is not None:
         out._lya_ids = ids_t            # keep the id buffer alive until the kernel ran
     return out
@@ -325,12 +346,13 @@ def rescale_mean_flux(tau, target: float, tol: float = 1e-12, max_iter: int = 50
     if flux_out is True:
         F = torch.empty_like(tau)
     elif flux_out is not None and flux_out is not False:
-        F = _require_cuda_f32(flux_out, "flux_out")
+        F = _check_out_like(tau, _require_cuda_f32(flux_out, "flux_out"), "flux_out")
     A = ctypes.c_double(math.nan)
-    _check(load_library().lya_rescale_mean_flux(tau.data_ptr(), tau.numel(), float(target), float(tol),
-                                                int(max_iter), ctypes.byref(A),
-                                                F.data_ptr() if F is not None else None,
-                                                _stream_handle(stream)), "lya_rescale_mean_flux")
+    with _on(tau):
+        _check(load_library().lya_rescale_mean_flux(tau.data_ptr(), tau.numel(), float(target), float(tol),
+                                                    int(max_iter), ctypes.byref(A),
+                                                    F.data_ptr() if F is not None else None,
+                                                    _stream_handle(stream)), "lya_rescale_mean_flux")
     return A.value, F
 
 
@@ -344,13 +366,15 @@ def rescale_mean_flux_stats(tau, target: float, tol: float = 1e-12, max_iter: in
     if flux_out is True:
         F = torch.empty_like(tau)
     elif flux_out is not None and flux_out is not False:
-        F = _require_cuda_f32(flux_out, "flux_out")
+        F = _check_out_like(tau, _require_cuda_f32(flux_out, "flux_out"), "flux_out")
     A = ctypes.c_double(math.nan)
     out = _FluxStats()
-    _check(load_library().lya_rescale_mean_flux_stats(tau.data_ptr(), tau.numel(), float(target), float(tol),
-                                                      int(max_iter), ctypes.byref(A),
-                                                      F.data_ptr() if F is not None else None, ctypes.byref(out),
-                                                      _stream_handle(stream)), "lya_rescale_mean_flux_stats")
+    with _on(tau):
+        _check(load_library().lya_rescale_mean_flux_stats(tau.data_ptr(), tau.numel(), float(target), float(tol),
+                                                          int(max_iter), ctypes.byref(A),
+                                                          F.data_ptr() if F is not None else None,
+                                                          ctypes.byref(out), _stream_handle(stream)),
+               "lya_rescale_mean_flux_stats")
     st = FluxStats(out.mean_flux, out.var_flux, out.tau_eff, np.array(out.pdf[:], dtype=np.int64), out.n)
     return A.value, F, st
 
@@ -364,12 +388,13 @@ def rescale_mean_flux_noalloc(tau, target: float, flux_out, tol: float = 1e-12, 
     """
     _require_cuda_f32(tau, "tau")
     if flux_out is not None:
-        _require_cuda_f32(flux_out, "flux_out")
+        _check_out_like(tau, _require_cuda_f32(flux_out, "flux_out"), "flux_out")
     A = ctypes.c_double(math.nan)
-    _check(load_library().lya_rescale_mean_flux_noalloc(
-        tau.data_ptr(), tau.numel(), float(target), float(tol), int(max_iter), ctypes.byref(A),
-        flux_out.data_ptr() if flux_out is not None else None, _stream_handle(stream)),
-        "lya_rescale_mean_flux_noalloc")
+    with _on(tau):
+        _check(load_library().lya_rescale_mean_flux_noalloc(
+            tau.data_ptr(), tau.numel(), float(target), float(tol), int(max_iter), ctypes.byref(A),
+            flux_out.data_ptr() if flux_out is not None else None, _stream_handle(stream)),
+            "lya_rescale_mean_flux_noalloc")
     return A.value
 
 
@@ -377,8 +402,9 @@ def tau_moments(tau, stream=None):
     """(sum tau, number of zeros, number of invalid values) of device values (lya_tau_moments)."""
     _require_cuda_f32(tau, "tau")
     out = (ctypes.c_double * 3)()
-    _check(load_library().lya_tau_moments(tau.data_ptr(), tau.numel(), out, _stream_handle(stream)),
-           "lya_tau_moments")
+    with _on(tau):
+        _check(load_library().lya_tau_moments(tau.data_ptr(), tau.numel(), out, _stream_handle(stream)),
+               "lya_tau_moments")
     return tuple(out)
 
 
@@ -386,8 +412,9 @@ def mean_flux_sums(tau, A: float, stream=None):
     """(sum e, sum tau e, sum tau^2 e), e = exp(-A tau), over device values (lya_mean_flux_sums)."""
     _require_cuda_f32(tau, "tau")
     out = (ctypes.c_double * 3)()
-    _check(load_library().lya_mean_flux_sums(tau.data_ptr(), tau.numel(), float(A), out,
-                                             _stream_handle(stream)), "lya_mean_flux_sums")
+    with _on(tau):
+        _check(load_library().lya_mean_flux_sums(tau.data_ptr(), tau.numel(), float(A), out,
+                                                 _stream_handle(stream)), "lya_mean_flux_sums")
     return tuple(out)
 
 
@@ -395,11 +422,10 @@ def flux_at(tau, A: float, out=None, stream=None):
     """F = exp(-A tau) on the device for a given A (lya_flux_at)."""
     _require_cuda_f32(tau, "tau")
     F = out if out is not None else _torch().empty_like(tau)
-    _require_cuda_f32(F, "out")
-    if F.numel() != tau.numel():
-        raise ValueError("out must have as many elements as tau")
-    _check(load_library().lya_flux_at(tau.data_ptr(), tau.numel(), float(A), F.data_ptr(),
-                                      _stream_handle(stream)), "lya_flux_at")
+    _check_out_like(tau, _require_cuda_f32(F, "out"), "out")
+    with _on(tau):
+        _check(load_library().lya_flux_at(tau.data_ptr(), tau.numel(), float(A), F.data_ptr(),
+                                          _stream_handle(stream)), "lya_flux_at")
     return F
 
 
@@ -416,8 +442,9 @@ def flux_stats(flux, stream=None) -> FluxStats:
     """<F>, Var F, tau_eff, 21-bin PDF of device flux values (lya_flux_stats)."""
     _require_cuda_f32(flux, "flux")
     out = _FluxStats()
-    _check(load_library().lya_flux_stats(flux.data_ptr(), flux.numel(), ctypes.byref(out),
-                                         _stream_handle(stream)), "lya_flux_stats")
+    with _on(flux):
+        _check(load_library().lya_flux_stats(flux.data_ptr(), flux.numel(), ctypes.byref(out),
+                                             _stream_handle(stream)), "lya_flux_stats")
     return FluxStats(out.mean_flux, out.var_flux, out.tau_eff, np.array(out.pdf[:], dtype=np.int64), out.n)
 
 

@@ -22,6 +22,7 @@
 #include <cstdint>
 #include <cstddef>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 
 #include "lya_device.cuh"
@@ -403,16 +404,23 @@ int grid_for(long long n)
 
 }  // namespace
 
+// SM count of the current device, cached per device (a relaxed atomic per
+// slot: concurrent first calls may both query, and store the same value).
 int sm_count()
 {
-    static int cached = 0;
-    if (!cached) {
-        int dev = 0, v = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-        cached = v > 0 ? v : 1;
+    constexpr int kMaxDev = 64;
+    static std::atomic<int> cached[kMaxDev];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (dev >= 0 && dev < kMaxDev) {
+        const int c = cached[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
     }
-    return cached;
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    v = v > 0 ? v : 1;
+    if (dev >= 0 && dev < kMaxDev) cached[dev].store(v, std::memory_order_relaxed);
+    return v;
 }
 
 size_t max_dynamic_smem()
@@ -571,21 +579,23 @@ done:
 
 // ---- allocation-free mean-flux root-find -------------------------------------------
 //
-// For callers that cannot allocate device memory: code running while a CUDA
-// graph is being captured into a pool they do not own, plug-ins whose host
+// For callers that cannot allocate device memory: plug-ins whose host
 // application forbids allocation after start-up, or callers on a memory
-// budget that is already fully handed out.  The Newton state and the per-CTA
-// partials live in a fixed file-scope device array instead of stream-ordered
-// allocations.  The array is kNoAllocScratchBytes (64 KiB) on every GPU that
-// loads the library and stays there until the process exits; it fits the
-// state plus kNoAllocMaxBlocks partials, so the reduction grid is capped at
-// kNoAllocMaxBlocks CTAs (the grid-stride loops still cover any n).
+// budget that is already fully handed out.  The root-find state and the
+// per-CTA partials live in a fixed file-scope device array instead of
+// stream-ordered allocations.  The array is kNoAllocScratchBytes (64 KiB) on
+// every GPU that loads the library and stays there until the process exits;
+// it fits the state plus kNoAllocMaxBlocks partials, so the reduction grid is
+// capped at kNoAllocMaxBlocks CTAs (the grid-stride loops still cover any n).
 //
-// Every call shares the one array and rewrites the whole state it reads (the
-// state is copied in from the host at the start of each call, and every
-// partial is written before it is read), so nothing is left over from a
-// previous call.  Two calls whose work overlaps on the GPU (different streams,
-// or different host threads on one device) race on the array.
+// Every call shares the one array.  Nothing carries over from an earlier
+// call: mf_state_init_kernel zeroes and sets the whole state at the start of
+// each call, and every CTA writes its partial before the last CTA reads them.
+// Two calls whose work overlaps on the GPU (different streams, or different
+// host threads on one device) race on the array.  Like the allocating
+// root-find, the call copies the state back and synchronises its stream after
+// every round of passes, so it cannot run while the stream is capturing a
+// CUDA graph.
 namespace lya {
 namespace {
 

@@ -85,3 +85,23 @@ def test_product_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "lya_oracle" not in text, f"{f} uses the oracle"
+
+
+def test_binding_refuses_a_short_or_foreign_flux_out_before_any_launch():
+    """The flux pass writes tau.numel() values into flux_out: the binding
+    checks its size and device on the host (meta tensors: no GPU, no launch)."""
+    import torch
+    from paper_1105_4747_gb300 import _binding as b
+    tau = torch.empty(100, device="meta")
+    with pytest.raises(ValueError, match="100 elements"):
+        b._check_out_like(tau, torch.empty(99, device="meta"), "flux_out")
+    assert b._check_out_like(tau, torch.empty(100, device="meta"), "flux_out") is not None
+
+    class Elsewhere:                   # a same-size buffer on another device
+        device = torch.device("cuda", 1)
+
+        @staticmethod
+        def numel():
+            return 100
+    with pytest.raises(ValueError, match="is on"):
+        b._check_out_like(tau, Elsewhere(), "flux_out")

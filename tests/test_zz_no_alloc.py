@@ -1,9 +1,12 @@
 """The allocation-free root-find gives the allocating one's answer.
 
 lya_rescale_mean_flux_noalloc serves callers that cannot allocate device
-memory (inside a CUDA-graph capture they do not own the pool of, plug-ins
-that must not allocate after start-up, services whose memory budget is spent);
-its scratch is a fixed device array inside liblya.  This file is named to be
+memory (plug-ins that must not allocate after start-up, services whose memory
+budget is spent); its scratch is a fixed device array inside liblya.  Besides
+the answers, the test reads the high watermark of the device's default
+stream-ordered memory pool (the pool the library's allocating calls draw
+from) through the driver API: it must not grow during a no-alloc call, and it
+does grow during the allocating call on the same input.  This file is named to be
 collected last, so a run that stops at the first failure has run every other
 test before it.
 """
@@ -26,6 +29,31 @@ def lya():
     __graft_entry__.build()
     import paper_1105_4747_gb300 as lya
     return lya
+
+
+_USED_MEM_HIGH = 8          # CU_MEMPOOL_ATTR_USED_MEM_HIGH (cuda.h)
+
+
+def _pool_high_watermark():
+    """(reset, read) callables for the used-memory high watermark of the
+    current device's default memory pool (driver API through ctypes)."""
+    import ctypes
+    cu = ctypes.CDLL("libcuda.so.1")
+    dev = ctypes.c_int()
+    assert cu.cuCtxGetDevice(ctypes.byref(dev)) == 0
+    pool = ctypes.c_void_p()
+    assert cu.cuDeviceGetDefaultMemPool(ctypes.byref(pool), dev) == 0
+
+    def reset():
+        zero = ctypes.c_uint64(0)
+        assert cu.cuMemPoolSetAttribute(pool, _USED_MEM_HIGH, ctypes.byref(zero)) == 0
+
+    def read():
+        v = ctypes.c_uint64()
+        assert cu.cuMemPoolGetAttribute(pool, _USED_MEM_HIGH, ctypes.byref(v)) == 0
+        return v.value
+
+    return reset, read
 
 
 def _check_pair(lya, tau, target):
@@ -54,6 +82,28 @@ def test_noalloc_matches_allocating_root_find_twice(lya):
     big = torch.rand(3_000_000, device="cuda", generator=g) ** 4 * 5.0
     _check_pair(lya, big, 0.7)
     _check_pair(lya, big, 0.7)
+
+
+def test_noalloc_draws_nothing_from_the_memory_pool(lya):
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(5)
+    tau = torch.rand(2_000_000, device="cuda", generator=g) ** 3 * 4.0
+    F = torch.empty_like(tau)
+    torch.cuda.synchronize()
+    reset, read = _pool_high_watermark()
+    # (a reset watermark starts at the pool's memory in use, normally 0)
+    for _ in range(2):
+        reset()
+        base = read()
+        lya.rescale_mean_flux_noalloc(tau, 0.75, F)
+        torch.cuda.synchronize()
+        assert read() == base
+    # the allocating call on the same input does draw from the pool
+    reset()
+    base = read()
+    lya.rescale_mean_flux(tau, 0.75, flux_out=F)
+    torch.cuda.synchronize()
+    assert read() > base
 
 
 def test_noalloc_errors_match(lya):
