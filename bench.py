@@ -315,9 +315,32 @@ def serve_stream(lya, srv, fields, reqs, t_end):
     return done, lag, int(t0 * 1e9)
 
 
-def run_serving(lya, torch, warm_s, measure_s, burst=400, budget=SERVE_BUDGET):
+# bytes per served pixel the step moves: Delta and v read (8), tau written and
+# read back by the init and two Halley passes (4 + 12), F written by the flux
+# pass after reading tau (8)
+SERVE_BYTES_PER_PX = 32
+
+
+def serving_pairs_per_px(specs, rows=16, T0=1.75e4, gamma=1.3, pivot=10.0):
+    """Algorithmic pairs per pixel of the served stream: every pool field's
+    pairs per pixel on a few host rows with the middle of the requests'
+    temperature range (T = T0 min(1 + delta, pivot)^(gamma - 1)), weighted
+    by skewer length (requests pick fields uniformly, so pixels go as n_pix)."""
+    num = den = 0.0
+    for sp in specs:
+        r, v, _ = ls.grid_rows(sp, np.arange(rows), with_temp=False)
+        T = T0 * np.minimum(r.astype(np.float64), pivot) ** (gamma - 1.0)
+        e = np.sqrt(sp.omega_m * (1 + sp.z) ** 3 + sp.omega_l)
+        du = 100.0 * e / (1 + sp.z) * sp.box / sp.n_pix
+        num += algorithmic_pairs_per_px(r, v, T, du) * sp.n_pix
+        den += sp.n_pix
+    return num / den
+
+
+def run_serving(lya, torch, warm_s, measure_s, burst=400, budget=SERVE_BUDGET, peaks=None, sms=152, clk_hz=2.07e9):
     """p50/p99 latency and served pixels/s of the Poisson stream, and the
-    loop's capacity (a burst of requests submitted at once)."""
+    loop's capacity (a burst of requests submitted at once) with its
+    rooflines."""
     specs, fields = serving_pool(lya, torch)
     reqs = ls.serve_requests(len(fields), int((warm_s + measure_s) * ls.SERVE_RATE * 1.5) + burst)
     srv = lya.Server(budget_bytes=budget, max_slots=256, step_target_us=2000.0)
@@ -359,12 +382,19 @@ def run_serving(lya, torch, warm_s, measure_s, burst=400, budget=SERVE_BUDGET):
     srv.close()
     for f in fields:
         f.close()
+    pairs_px = serving_pairs_per_px(specs)
+    hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    roofline = {"fp32_pipe": fp32_pipe(pairs_px, 1.0, 1e3 / cap, sms, clk_hz), "alg_pairs_per_px": pairs_px,
+                "hbm": {"achieved": cap * SERVE_BYTES_PER_PX / 1e9, "peak": hbm, "unit": "GB/s",
+                        "frac": cap * SERVE_BYTES_PER_PX / 1e9 / hbm, "bytes_per_px": SERVE_BYTES_PER_PX},
+                "at": "capacity (the burst), whole served step: extraction, root-find and statistics"}
     return {"workload": f"poisson_{ls.SERVE_RATE:g}rps_pool{len(fields)}x{ls.SERVE_SKEWERS_PER_FIELD}",
             "rate_rps": ls.SERVE_RATE, "warmup_s": warm_s, "measure_s": measure_s, "requests": n_meas,
             "failed": failed, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
             "served_px_per_s": px_done / measure_s, "offered_px_per_s": px_offered / measure_s,
-            "capacity_px_per_s": cap, "capacity_burst_requests": len(tail),
+            "capacity_px_per_s": cap, "capacity_burst_requests": len(tail), "roofline": roofline,
+            "p99_samples": int(len(lat)), "p99_tail_samples": int(round(0.01 * len(lat))),
             "submit_lag_p99_ms": float(np.percentile(np.array(lag), 99) * 1e3),
             "steps": info1["steps"] - info0["steps"], "gpu_launches": launches,
             "group_shift_by_n_pix": {str(k): v for k, v in shifts.items()},
@@ -557,6 +587,140 @@ def run_e2e(lya, torch, field, spec, S, params, target, rho, v, t, tau, F, n_ste
             "pipeline": "two device fields and two F buffers: H2D of step k+1 and D2H of step k-1 overlap step k"}
 
 
+def fp64_mean_flux(torch, tau, A):
+    """<exp(-A tau)> over every value of a device tensor in FP64 (torch, on the
+    device, chunk by chunk): the defining property of A, reported beside it."""
+    flat = tau.reshape(-1)
+    total = torch.zeros((), dtype=torch.float64, device=flat.device)
+    for lo in range(0, flat.numel(), 1 << 27):
+        total += torch.exp(-A * flat[lo:lo + (1 << 27)].double()).sum()
+    return float(total) / flat.numel()
+
+
+def measure_link(torch, nbytes=1 << 30, reps=5):
+    """Pinned host <-> device copy bandwidth (GB/s, best of reps, CUDA events):
+    one way each, and both ways at once on two streams."""
+    n = nbytes // 4
+    h_in = torch.empty(n, dtype=torch.float32).pin_memory()
+    h_out = torch.empty(n, dtype=torch.float32).pin_memory()
+    d_in = torch.empty(n, dtype=torch.float32, device="cuda")
+    d_out = torch.empty(n, dtype=torch.float32, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def timed(fn):
+        best = float("inf")
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            best = min(best, time.perf_counter() - t0)
+        return best
+
+    def both():
+        with torch.cuda.stream(s1):
+            d_in.copy_(h_in, non_blocking=True)
+        with torch.cuda.stream(s2):
+            h_out.copy_(d_out, non_blocking=True)
+
+    h2d = nbytes / timed(lambda: d_in.copy_(h_in, non_blocking=True)) / 1e9
+    d2h = nbytes / timed(lambda: h_out.copy_(d_out, non_blocking=True)) / 1e9
+    bi = 2 * nbytes / timed(both) / 1e9
+    del h_in, h_out, d_in, d_out
+    return {"h2d_gbs": h2d, "d2h_gbs": d2h, "both_ways_gbs": bi, "bytes_per_copy": nbytes,
+            "how": "pinned host memory, 1 GiB copies, best of 5, host clock around synchronised copies"}
+
+
+def fp32_pipe(pairs_px, n_px, ms, sms, clk_hz):
+    """Algorithmic pair arithmetic of an extraction against the FP32 pipe peak."""
+    peak = sms * 128 * clk_hz
+    achieved = pairs_px * n_px * FP32_OPS_PER_PAIR / (ms / 1e3)
+    return {"achieved": achieved, "peak": peak, "unit": "FP32 operations/s", "frac": achieved / peak}
+
+
+def time_extract(lya, torch, field, params, out, reps):
+    """Mean duration (ms, CUDA events) of extract_skewers over reps launches."""
+    lya.extract_skewers(field, params, out=out)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    for _ in range(reps):
+        lya.extract_skewers(field, params, out=out)
+    ev[1].record()
+    ev[1].synchronize()
+    return ev[0].elapsed_time(ev[1]) / reps
+
+
+def run_precision_variants(lya, torch, field, spec, S, tau_ms_comp, pairs_px, sms, clk_hz, reps):
+    """The optical depth of the same field with FP32 naive sums and with the
+    FP64 comparator kernel, beside the FP32-compensated product path."""
+    n_px = S * spec.n_pix
+    out = torch.empty((S, spec.n_pix), dtype=torch.float32, device="cuda")
+    ms_naive = time_extract(lya, torch, field, lya.ExtractParams(t_mode=0, precision=lya.PREC_F32_NAIVE), out, reps)
+    ms_f64 = time_extract(lya, torch, field, lya.ExtractParams(t_mode=0, precision=lya.PREC_F64), out, max(2, reps // 4))
+    del out
+    res = {}
+    for name, ms in (("f32_compensated", tau_ms_comp), ("f32_naive", ms_naive), ("f64", ms_f64)):
+        res[name] = {"ms": ms, "px_per_s": n_px / (ms / 1e3), "fp32_pipe": fp32_pipe(pairs_px, n_px, ms, sms, clk_hz)}
+    res["compensated_over_f64"] = ms_f64 / tau_ms_comp
+    res["note"] = ("optical-depth kernel alone, same 65,536 x 4,096 field; f64 is the plain FP64 comparator kernel "
+                   "(FP64 sums and exponentials, all pairs of the skewer's widest window); FP32-pipe fraction = "
+                   "algorithmic pairs x 6 FP32 operations / duration / (SMs x 128 x max clock)")
+    return res
+
+
+def run_grid_object(lya, torch, steps, warmup, peaks, sms, clk_hz):
+    """The 1536^3 grid (config 4): every one of its 2,359,296 rows x 1,536 px
+    in one optical-depth launch, then the root-find and statistics, timed
+    like the headline step."""
+    spec, S, target = ls.GRID_1536, ls.GRID_1536_ROWS, ls.GRID_1536_FT
+    rho, v, t = ls.grid_on_device(spec, S, torch)          # 43.5 GB on the device
+    field = lya.Field(rho, v, t, box=spec.box, z=spec.z, borrow=True)
+    params = lya.ExtractParams(t_mode=0)
+    tau = torch.empty((S, spec.n_pix), dtype=torch.float32, device="cuda")
+    F = torch.empty_like(tau)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        lya.extract_skewers(field, params, out=tau)
+        A, _, st = lya.rescale_mean_flux_stats(tau, target, flux_out=F)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    clocks.start()
+    for e in evs:
+        e[0].record(stream)
+        lya.extract_skewers(field, params, out=tau)
+        e[1].record(stream)
+        A, _, st = lya.rescale_mean_flux_stats(tau, target, flux_out=F)
+        e[2].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = statistics.mean(e[0].elapsed_time(e[2]) for e in evs)
+    tau_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    field.status()
+    n_px = S * spec.n_pix
+    r64, v64, t64 = ls.grid_rows(spec, np.arange(64))
+    pairs_px = algorithmic_pairs_per_px(r64, v64, t64, lya.field_pixel_width(field))
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    achieved = ALG_BYTES_PER_PX * n_px / (tau_ms / 1e3) / 1e9
+    per_row, profiled_hash = TAU_DRAM_PROFILE["grid1536"]
+    mean_flux = fp64_mean_flux(torch, tau, A)
+    field.close()
+    del rho, v, t, tau, F
+    torch.cuda.empty_cache()
+    return {"workload": "grid_1536cubed_z2.3: all 2,359,296 rows x 1,536 px of a periodic 1536^3 grid "
+                        "(1 h^-1 Gpc, T0 = 2e4 K, gamma = 1.4), one launch", "value": n_px / (ms / 1e3),
+            "unit": UNIT, "ms_per_step": ms, "steps": steps, "A": A, "mean_flux": mean_flux,
+            "stats_mean_flux": st.mean_flux, "target_mean_flux": target,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": per_row * S if tau_code_hash() == profiled_hash else None,
+                         "kernel_ms": tau_ms, "alg_bytes_per_launch": ALG_BYTES_PER_PX * n_px},
+            "pipes": {"alg_pairs_per_px": pairs_px,
+                      "fp32_pipe": fp32_pipe(pairs_px, n_px, tau_ms, sms, clk_hz)},
+            "clocks": clk, "parity": "tests/test_gpu_grid.py: 512 random rows (seed 1004) against the FP64 oracle",
+            "l2": "inputs 43.5 GB > 129 MB L2: no flush between steps"}
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -642,6 +806,13 @@ def run_ours(args):
         e2e = run_e2e(lya, torch, field, spec, S, params, target, rho, v, t, tau, F,
                       max(3, min(args.steps, 8)), world, local)
         del rho, v, t
+        # the host link bounds e2e: its measured bandwidth and e2e's use of it
+        link = measure_link(torch)
+        step_s = e2e["ms_per_step"] / 1e3
+        e2e["link"] = link
+        e2e["link_frac"] = {"h2d": e2e["h2d_bytes_per_step"] / step_s / 1e9 / link["h2d_gbs"],
+                            "d2h": e2e["d2h_bytes_per_step"] / step_s / 1e9 / link["d2h_gbs"],
+                            "note": "bytes per step / e2e time per step / the measured one-way bandwidth"}
 
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
@@ -669,6 +840,15 @@ def run_ours(args):
              "unit": "operations/s", "peak_clock_mhz": clk_hz / 1e6, "sms": sms,
              "ncu_pipe_pct": pipe_ncu if pipe_ncu and tau_code_hash() == pipe_hash else None}
 
+    # A's defining property over all pixels, in FP64 (the root-find stops at
+    # |<exp(-A tau)> - target| <= 1e-12)
+    mean_flux = fp64_mean_flux(torch, tau, A)
+
+    precision = None
+    if not grid and not args.no_precision:
+        precision = run_precision_variants(lya, torch, field, spec, S, tau_ms, pairs_px, sms, clk_hz,
+                                           max(3, args.steps))
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not grid:
         cpu = oracle_timing(spec, args.cpu_seconds)
@@ -678,18 +858,26 @@ def run_ours(args):
         del tau, F
         torch.cuda.empty_cache()
         serving = run_serving(lya, torch, 2.0, args.serve_seconds, burst=args.serve_burst,
-                              budget=int(args.serve_budget_gb * (1 << 30)))
+                              budget=int(args.serve_budget_gb * (1 << 30)), peaks=peaks, sms=sms, clk_hz=clk_hz)
+    field.close()
+
+    grid_obj = None
+    if not grid and not args.no_grid:
+        torch.cuda.empty_cache()
+        grid_obj = run_grid_object(lya, torch, max(3, min(args.steps, 5)), 2, peaks, sms, clk_hz)
 
     if rank == 0:
         line = {"metric": METRIC, "value": world * n_px / (ms / 1e3), "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": workload_config(spec, S, {"parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
-                                                    "A": A, "mean_flux": st.mean_flux}, grid),
-                "roofline": roofline, "pipes": pipes, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "serving": serving, "post": post}
+                                                    "A": A, "mean_flux": mean_flux,
+                                                    "mean_flux_definition": "<exp(-A tau)> over all pixels in FP64",
+                                                    "stats_mean_flux": st.mean_flux}, grid),
+                "roofline": roofline, "pipes": pipes, "precision_variants": precision, "cpu_baseline": cpu,
+                "e2e": e2e, "gpu_launches": launches, "clocks": clk, "serving": serving, "grid1536": grid_obj,
+                "post": post}
         print(json.dumps(line), flush=True)
-    field.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -735,8 +923,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-post", action="store_true", help="skip the mock-spectrum and flux-power timings")
-    ap.add_argument("--serve-seconds", type=float, default=10.0,
-                    help="measured seconds of the Poisson request stream in the default run")
+    ap.add_argument("--no-grid", action="store_true", help="skip the 1536^3 grid object of the default run")
+    ap.add_argument("--no-precision", action="store_true", help="skip the naive and FP64 kernel timings")
+    ap.add_argument("--serve-seconds", type=float, default=52.0,
+                    help="measured seconds of the Poisson request stream in the default run (>= 10,000 requests)")
     ap.add_argument("--serve-burst", type=int, default=400, help="requests of the capacity burst")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0, help="serving memory budget (GiB)")
     args = ap.parse_args()

@@ -73,7 +73,9 @@ enum {
     LYA_SRC_DEVICE_COPY = 1,   /* device memory: copied into field-owned memory */
     LYA_SRC_DEVICE_BORROW = 2  /* device memory: referenced, not copied; the
                                   caller keeps it alive and unchanged while the
-                                  field exists (create only)                   */
+                                  field exists (create only); each array must
+                                  start on a 16-byte boundary (LYA_EINVAL
+                                  otherwise)                                   */
 };
 
 /* Accumulation precision of the pair sum (Eq. 6). */
@@ -227,18 +229,72 @@ lya_status lya_rescale_mean_flux_stats(const float* tau, int64_t n, double targe
 /*
  * Per-device shares of the mean-flux root-find (Sec. 2.3) when one request's
  * pixels are split over several devices or processes: each computes its
- * share, the caller sums the shares over all parts (an all-reduce of three
- * numbers) and steps A itself, then writes F with lya_flux_at.
+ * share, the shares are summed over all parts (an all-reduce of three
+ * numbers) and stepped with lya_mean_flux_step below, then each part writes
+ * its F with lya_flux_at (lya_rescale_mean_flux_sharded does all of it).
  *   lya_tau_moments:    out = { sum tau, number of tau == 0, number of
  *                       negative or non-finite tau } over n device values.
- *   lya_mean_flux_sums: out = { sum e, sum tau e, sum tau^2 e }, e = exp(-A tau),
- *                       in FP64 (the terms in FP32, see lya_rescale_mean_flux).
+ *   lya_mean_flux_sums: out = { sum e, sum tau e, sum tau^2 e }, e = exp(-A tau):
+ *                       sum e to ~1e-13 relative (double-float exponentials,
+ *                       FP64 sums), the other two in compensated FP32 / FP64.
  *   lya_flux_at:        flux_out[i] = exp(-A tau[i]) (device, n floats).
  * The first two synchronise the stream; A must be finite and >= 0.
  */
 lya_status lya_tau_moments(const float* tau, int64_t n, double out[3], void* stream);
 lya_status lya_mean_flux_sums(const float* tau, int64_t n, double A, double out[3], void* stream);
 lya_status lya_flux_at(const float* tau, int64_t n, double A, float* flux_out, void* stream);
+
+/*
+ * The Sec. 2.3 iteration for a request split over several parts, stepped on
+ * the host from the parts' summed shares (no device work; every part holds
+ * its own copy and takes the same steps from the same sums):
+ *   lya_mean_flux_start: totals = { sum tau, number of tau == 0, number of
+ *     invalid tau, number of values } over all parts (each part's
+ *     lya_tau_moments and its n, summed); target in (0, 1), tol > 0,
+ *     max_iter >= 1.  Starts Newton at the Jensen bound A0 = -ln(target)/<tau>
+ *     (below the root).  LYA_EINVAL for an invalid value or all tau = 0,
+ *     LYA_ENOCONV when no A reaches the target (too many tau = 0); the
+ *     iteration is then already done with that status.
+ *   lya_mean_flux_step: sums = { sum e, sum tau e, sum tau^2 e } at it->A over
+ *     all parts (each part's lya_mean_flux_sums, summed), e = exp(-A tau).
+ *     One safeguarded step (Halley, else Newton, else bisection inside the
+ *     bracket).  The iteration ends (it->done, it->status = LYA_OK) when
+ *     |<e> - target| <= tol at it->A, or when Taylor's bound certifies that
+ *     the Newton step lands within tol (it->A is then that point and it->g
+ *     the bound), or when the step stalls at FP64 resolution; it ends with
+ *     LYA_ENOCONV after max_iter steps.  Returns it->status once done, else
+ *     LYA_OK.
+ */
+typedef struct {
+    double A;            /* current A (the final one once done)                  */
+    double lo, hi;       /* bracket of the root                                  */
+    double g;            /* last <e> - target, or the certified bound on |g|     */
+    int iter, max_iter;  /* steps taken, step limit                              */
+    int done;            /* 1 once the iteration has ended                       */
+    lya_status status;   /* LYA_OK when converged; the error otherwise          */
+    double target, tol, n;   /* target <F>, tolerance, values over all parts    */
+} lya_mean_flux_iter;
+
+lya_status lya_mean_flux_start(const double totals[4], double target, double tol, int max_iter,
+                               lya_mean_flux_iter* it);
+lya_status lya_mean_flux_step(lya_mean_flux_iter* it, const double sums[3]);
+
+/*
+ * The whole split root-find in one call per part (Sec. 2.3): every part calls
+ * it with its own n device values tau (n may be 0), the same target, tol and
+ * max_iter, and an all-reduce callback that replaces values[0 .. count) by
+ * their sums over all parts (and returns 0; anything else ends the call with
+ * LYA_ECUDA).  The library computes the shares, sums them with the callback
+ * (one call of 4 values, then one of 3 values per step) and steps the
+ * iteration as lya_mean_flux_step; *A_out (identical on every part) and
+ * *iters_out (nullable) receive the result, flux_out (device, n floats,
+ * nullable) this part's F = exp(-A tau).  Errors as lya_rescale_mean_flux.
+ * Synchronises the stream.
+ */
+typedef int (*lya_allreduce_fn)(double* values, int count, void* user);
+lya_status lya_rescale_mean_flux_sharded(const float* tau, int64_t n, double target, double tol, int max_iter,
+                                         lya_allreduce_fn allreduce, void* user, double* A_out, int* iters_out,
+                                         float* flux_out, void* stream);
 
 /*
  * Flux statistics (Sec. 2.3, Sec. 5.2) over n device values F: mean,

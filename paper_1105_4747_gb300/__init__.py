@@ -34,6 +34,10 @@ from ._binding import (  # noqa: F401
     flux_at,
     flux_stats,
     mean_flux_sums,
+    mean_flux_start,
+    mean_flux_step,
+    MeanFluxIter,
+    rescale_mean_flux_sharded,
     tau_moments,
     kernel_launches,
     library_path,

@@ -71,6 +71,16 @@ class _SightlineDesc(ctypes.Structure):
                 ("sigma_delta", ctypes.c_double), ("k_f", ctypes.c_double), ("seed", ctypes.c_uint64)]
 
 
+class _MeanFluxIter(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_double), ("lo", ctypes.c_double), ("hi", ctypes.c_double), ("g", ctypes.c_double),
+                ("iter", ctypes.c_int), ("max_iter", ctypes.c_int), ("done", ctypes.c_int), ("status", ctypes.c_int),
+                ("target", ctypes.c_double), ("tol", ctypes.c_double), ("n", ctypes.c_double)]
+
+
+# int allreduce(double* values, int count, void* user): values summed over all parts, in place
+_ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_void_p)
+
+
 class _ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int),
                 ("step_target_us", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int)]
@@ -130,6 +140,10 @@ def load_library():
         lib.lya_tau_moments.argtypes = [vp, i64, ctypes.POINTER(d), vp]
         lib.lya_mean_flux_sums.argtypes = [vp, i64, d, ctypes.POINTER(d), vp]
         lib.lya_flux_at.argtypes = [vp, i64, d, vp, vp]
+        lib.lya_mean_flux_start.argtypes = [ctypes.POINTER(d), d, d, i32, ctypes.POINTER(_MeanFluxIter)]
+        lib.lya_mean_flux_step.argtypes = [ctypes.POINTER(_MeanFluxIter), ctypes.POINTER(d)]
+        lib.lya_rescale_mean_flux_sharded.argtypes = [vp, i64, d, d, i32, _ALLREDUCE_FN, vp, ctypes.POINTER(d),
+                                                      ctypes.POINTER(i32), vp, vp]
         u64 = ctypes.c_uint64
         lib.lya_field_pixel_width.argtypes = [vp, ctypes.POINTER(d)]
         lib.lya_generate_sightlines.argtypes = [ctypes.POINTER(_SightlineDesc), i64, i64, i64, vp, vp, vp]
@@ -150,7 +164,8 @@ def load_library():
         for name in ("lya_create_field", "lya_field_load", "lya_destroy_field", "lya_field_status",
                      "lya_field_shape", "lya_extract_skewers", "lya_rescale_mean_flux",
                      "lya_rescale_mean_flux_noalloc", "lya_rescale_mean_flux_stats", "lya_flux_stats", "lya_tau_moments",
-                     "lya_mean_flux_sums", "lya_flux_at", "lya_server_create", "lya_server_autotune",
+                     "lya_mean_flux_sums", "lya_flux_at", "lya_mean_flux_start", "lya_mean_flux_step",
+                     "lya_rescale_mean_flux_sharded", "lya_server_create", "lya_server_autotune",
                      "lya_server_submit", "lya_server_poll", "lya_server_wait", "lya_server_copy_flux",
                      "lya_server_release", "lya_server_info", "lya_server_destroy", "lya_field_pixel_width",
                      "lya_mock_shape", "lya_mock_spectra", "lya_flux_power_1d", "lya_generate_sightlines",
@@ -427,6 +442,74 @@ def flux_at(tau, A: float, out=None, stream=None):
         _check(load_library().lya_flux_at(tau.data_ptr(), tau.numel(), float(A), F.data_ptr(),
                                           _stream_handle(stream)), "lya_flux_at")
     return F
+
+
+class MeanFluxIter:
+    """The Sec. 2.3 iteration of a split request, stepped by the library on
+    the host (lya_mean_flux_iter): ``A``, ``done``, ``status``, ``iter``, ``g``."""
+
+    def __init__(self, c: _MeanFluxIter):
+        self._c = c
+
+    def __getattr__(self, name):
+        return getattr(self._c, name)
+
+
+def mean_flux_start(totals, target: float, tol: float = 1e-12, max_iter: int = 50) -> MeanFluxIter:
+    """lya_mean_flux_start from totals = (sum tau, zeros, invalid, n) over all
+    parts.  Raises LyaError when the iteration cannot start."""
+    it = _MeanFluxIter()
+    t = (ctypes.c_double * 4)(*[float(x) for x in totals])
+    _check(load_library().lya_mean_flux_start(t, float(target), float(tol), int(max_iter), ctypes.byref(it)),
+           "lya_mean_flux_start")
+    return MeanFluxIter(it)
+
+
+def mean_flux_step(it: MeanFluxIter, sums) -> bool:
+    """lya_mean_flux_step with sums = (sum e, sum tau e, sum tau^2 e) at it.A
+    over all parts; returns True once the iteration has ended.  Raises
+    LyaError if it ended without converging."""
+    v = (ctypes.c_double * 3)(*[float(x) for x in sums])
+    _check(load_library().lya_mean_flux_step(ctypes.byref(it._c), v), "lya_mean_flux_step")
+    return bool(it.done)
+
+
+def rescale_mean_flux_sharded(tau, target: float, allreduce, tol: float = 1e-12, max_iter: int = 50,
+                              flux_out=True, stream=None):
+    """lya_rescale_mean_flux_sharded: this part's tau (CUDA tensor, may be
+    empty) and ``allreduce(list_of_floats) -> list_of_floats`` summing over
+    all parts.  Returns (A, steps, F of this part or None)."""
+    torch = _torch()
+    _require_cuda_f32(tau, "tau")
+    F = None
+    if flux_out is True:
+        F = torch.empty_like(tau)
+    elif flux_out is not None and flux_out is not False:
+        F = _check_out_like(tau, _require_cuda_f32(flux_out, "flux_out"), "flux_out")
+    errors = []
+
+    def cb(ptr, count, _user):
+        try:
+            out = allreduce([ptr[k] for k in range(count)])
+            for k in range(count):
+                ptr[k] = float(out[k])
+            return 0
+        except Exception as exc:             # surfaced after the call
+            errors.append(exc)
+            return 1
+
+    fn = _ALLREDUCE_FN(cb)
+    A = ctypes.c_double(math.nan)
+    it = ctypes.c_int(0)
+    with _on(tau):
+        status = load_library().lya_rescale_mean_flux_sharded(
+            tau.data_ptr() if tau.numel() else None, tau.numel(), float(target), float(tol), int(max_iter), fn,
+            None, ctypes.byref(A), ctypes.byref(it), F.data_ptr() if (F is not None and tau.numel()) else None,
+            _stream_handle(stream))
+    if errors:
+        raise errors[0]
+    _check(status, "lya_rescale_mean_flux_sharded")
+    return A.value, it.value, F
 
 
 @dataclass

@@ -195,6 +195,9 @@ lya_status make_tau_launch(lya_field f, const lya_extract_params* p, TauLaunch* 
     L.T0 = (float)p->T0;
     L.gm1 = (float)(p->gamma - 1.0);
     L.pivot = std::isfinite(p->delta_pivot) ? (float)p->delta_pivot : INFINITY;
+    L.lT0 = (float)std::log2(p->T0 * 1e-4);
+    L.lpivot = std::isfinite(p->delta_pivot) ? (float)std::log2(p->delta_pivot) : INFINITY;
+    L.lK = (float)std::log2(ph.K);
     L.du_d = ph.du;
     L.inv_du_d = 1.0 / ph.du;
     L.c_coef_d = std::sqrt(kLog2e) / ph.b1e4;
@@ -239,6 +242,11 @@ lya_status lya_create_field(const lya_field_desc* desc, const float* rho, const 
     if ((desc->has_temp != 0) != (temp != nullptr)) return LYA_EINVAL;
     if (src != LYA_SRC_HOST && src != LYA_SRC_DEVICE_COPY && src != LYA_SRC_DEVICE_BORROW) return LYA_EINVAL;
     if (desc->n_skewers > INT64_MAX / desc->n_pix) return LYA_EINVAL;
+    // a borrowed array is read with 16-byte vector loads and bulk copies
+    if (src == LYA_SRC_DEVICE_BORROW &&
+        ((reinterpret_cast<uintptr_t>(rho) | reinterpret_cast<uintptr_t>(vpec) | reinterpret_cast<uintptr_t>(temp)) &
+         15) != 0)
+        return LYA_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     lya_field f = new (std::nothrow) lya_field_s();
     if (!f) return LYA_ENOMEM;
@@ -373,6 +381,32 @@ lya_status lya_flux_at(const float* tau, int64_t n, double A, float* flux_out, v
 {
     if (!tau || n <= 0 || !flux_out || !(A >= 0.0) || !std::isfinite(A)) return LYA_EINVAL;
     return lya::flux_at_run(tau, n, A, flux_out, static_cast<cudaStream_t>(stream));
+}
+
+lya_status lya_mean_flux_start(const double totals[4], double target, double tol, int max_iter,
+                               lya_mean_flux_iter* it)
+{
+    if (!totals || !it || !(target > 0.0 && target < 1.0) || !(tol > 0.0) || max_iter < 1) return LYA_EINVAL;
+    if (!(totals[3] > 0.0) || !std::isfinite(totals[0]) || !(totals[1] >= 0.0) || !(totals[2] >= 0.0))
+        return LYA_EINVAL;
+    return lya::mean_flux_start(totals, target, tol, max_iter, it);
+}
+
+lya_status lya_mean_flux_step(lya_mean_flux_iter* it, const double sums[3])
+{
+    if (!it || !sums || !(it->n > 0.0)) return LYA_EINVAL;
+    if (!std::isfinite(sums[0]) || !std::isfinite(sums[1]) || !std::isfinite(sums[2])) return LYA_EINVAL;
+    return lya::mean_flux_step(it, sums);
+}
+
+lya_status lya_rescale_mean_flux_sharded(const float* tau, int64_t n, double target, double tol, int max_iter,
+                                         lya_allreduce_fn allreduce, void* user, double* A_out, int* iters_out,
+                                         float* flux_out, void* stream)
+{
+    if (n < 0 || (n > 0 && !tau) || !allreduce || !A_out) return LYA_EINVAL;
+    if (!(target > 0.0 && target < 1.0) || !(tol > 0.0) || max_iter < 1) return LYA_EINVAL;
+    return lya::mean_flux_sharded(tau, n, target, tol, max_iter, allreduce, user, A_out, iters_out, flux_out,
+                                  static_cast<cudaStream_t>(stream));
 }
 
 lya_status lya_field_pixel_width(lya_field f, double* du_kms)

@@ -46,6 +46,51 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes)
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// ---- 1D bulk copies (the TMA engine) into shared memory --------------------------
+// cp.async.bulk moves a contiguous run of global memory into this CTA's shared
+// memory; an mbarrier counts the bytes that have landed (complete_tx).  Both
+// addresses must be 16-byte aligned and the size a multiple of 16.
+__device__ __forceinline__ unsigned smem_addr(const void* p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+// Waits for the phase of parity `parity` of bar to complete; gives up after
+// `spins` polls (each poll may suspend the thread for a while) and returns
+// false, so a copy that never lands cannot hang the kernel.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, unsigned spins)
+{
+    for (unsigned k = 0; k < spins; ++k) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 // Kahan-compensated FP32 accumulator.  The adds are written with explicit
 // round-to-nearest intrinsics so the compiler can neither contract nor
 // reassociate them.

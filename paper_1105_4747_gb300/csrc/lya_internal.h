@@ -56,6 +56,9 @@ struct TauLaunch {
     float h_coef;             // nsigma * sqrt(log2 e): window half-width = h_coef / a
     float K;                  // Eq. 6 prefactor times Eq. 4 constants (see api)
     float T0, gm1, pivot;     // power law: T = T0 min(rho, pivot)^gm1
+    float lT0;                // log2(T0 / 1e4 K)
+    float lpivot;             // log2(pivot) (+inf: no pivot)
+    float lK;                 // log2(K)
     // FP64 forms (the FP64 comparator kernel)
     double du_d, inv_du_d, c_coef_d, h_coef_d, K_d, T0_d, gm1_d, pivot_d;
 };
@@ -66,6 +69,8 @@ lya_status make_tau_launch(lya_field f, const lya_extract_params* p, TauLaunch* 
 
 // Launch the optical-depth kernel for the requested precision.
 cudaError_t launch_tau(const TauLaunch& L, int precision, cudaStream_t stream);
+
+
 
 // Shared-memory bytes the optical-depth kernel needs for n_pix pixels and a
 // window bound w_max (the kernel variant is chosen by what fits).
@@ -92,6 +97,15 @@ lya_status mean_flux_solve_noalloc(const float* tau, int64_t n, double target, d
 lya_status tau_moments_run(const float* tau, int64_t n, double* out3, cudaStream_t stream);
 lya_status mean_flux_sums_run(const float* tau, int64_t n, double A, double* out3, cudaStream_t stream);
 lya_status flux_at_run(const float* tau, int64_t n, double A, float* flux, cudaStream_t stream);
+
+// The split root-find's host steps (lya_mean_flux_start / _step) and its
+// whole driver with an all-reduce callback (lya_rescale_mean_flux_sharded).
+lya_status mean_flux_start(const double totals[4], double target, double tol, int max_iter,
+                           lya_mean_flux_iter* it);
+lya_status mean_flux_step(lya_mean_flux_iter* it, const double sums[3]);
+lya_status mean_flux_sharded(const float* tau, int64_t n, double target, double tol, int max_iter,
+                             lya_allreduce_fn allreduce, void* user, double* A_out, int* iters_out, float* flux_out,
+                             cudaStream_t stream);
 
 // Flux statistics (Sec. 2.3, 5.2) over n device flux values.
 lya_status flux_stats_run(const float* flux, int64_t n, lya_flux_stats_t* out,

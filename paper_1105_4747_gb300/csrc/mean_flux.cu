@@ -12,12 +12,14 @@
 // and updates A in device memory, so passes chain on the stream without a
 // host round trip.  A pass launched after convergence returns at once.
 //
-// Precision: the per-pixel exponential is FP32 (MUFU ex2) of a double-float
-// argument y = tau * A log2(e) = y_hi + y_lo, i.e. e = 2^-y_hi (1 - y_lo ln 2);
-// each thread accumulates in compensated FP32, CTAs and the final sum in FP64.
-// The 2^-y_hi part and its first-order correction are summed separately, so
-// g(A) stays smooth in A far below FP32 resolution and the FP64 Newton can
-// reach |g| <= 1e-12.
+// Precision: the first Halley pass of a round and the flux pass use the MUFU
+// exponential of a double-float argument y = tau A log2(e) = y_hi + y_lo,
+// e = 2^-y_hi (1 - y_lo ln 2), summed in compensated FP32 (g to ~1e-7: a fast
+// start that never ends the iteration; F itself is FP32).  The second Halley
+// pass forms e in double-float arithmetic to ~1e-15 (exp2_neg_precise) and
+// sums it in float pairs flushed to FP64, so g is known to ~1e-13; it ends the
+// iteration when |g| <= tol (1e-12) or when its Newton step is certified to
+// land within tol (halley_update).  CTAs and the final sums are FP64.
 #include <cmath>
 #include <cstdint>
 #include <cstddef>
@@ -48,6 +50,7 @@ __global__ void __launch_bounds__(kThreads) mf_init_kernel(const float* __restri
     while ((n >> 22) > smask) smask = 2 * smask + 1;        // sample stride - 1 (a power of 2 minus 1)
     KahanF32 s;
     unsigned int z = 0, bad = 0;                            // per thread: far below 2^32 values
+    float tmax = 0.f;
     auto take = [&](float t) {
         if (!(t >= 0.f) || !isfinite(t)) {
             ++bad;
@@ -55,6 +58,7 @@ __global__ void __launch_bounds__(kThreads) mf_init_kernel(const float* __restri
         }
         s.add(t);
         z += (t == 0.f);
+        tmax = fmaxf(tmax, t);
     };
     auto sample = [&](float t) {
         if (t >= 0.f && isfinite(t)) atomicAdd(&h_s[t == 0.f ? kHistBins : hist_bin(t)], 1u);
@@ -101,6 +105,8 @@ __global__ void __launch_bounds__(kThreads) mf_init_kernel(const float* __restri
     __shared__ double sh[3][32];
     double v[3] = {(double)s.value(), (double)z, (double)bad};
     block_sum<3>(v, sh);
+    for (int o = 16; o > 0; o >>= 1) tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&st->tau_max_bits, __float_as_uint(tmax));
     for (int b = threadIdx.x; b <= kHistBins; b += blockDim.x)
         if (h_s[b]) atomicAdd(&st->hist[b], (unsigned long long)h_s[b]);
     if (threadIdx.x == 0) part[blockIdx.x] = Partial{v[0], 0.0, 0.0, 0.0, (long long)v[1], (long long)v[2]};
@@ -134,25 +140,53 @@ __global__ void __launch_bounds__(kThreads) mf_state_init_kernel(MFState* st, do
 }
 
 // ---- one Halley pass: g, g' and g'' in one read of tau -----------------------------
+// PRECISE: sum e in double-float (exp2_neg_precise), so g is known to ~1e-13
+// and the pass may end the iteration; else the MUFU exponential with its
+// first-order argument correction (g to ~1e-7), a fast start.
+template <bool PRECISE>
 __global__ void __launch_bounds__(kThreads) mf_newton_kernel(const float* __restrict__ tau, long long n,
                                                            MFState* st, Partial* part)
 {
     if (st->done) return;
+    __shared__ float2 tab[PRECISE ? kExp2TabSize : 1];
+    if constexpr (PRECISE) load_exp2_table(tab);
     float a_hi, a_lo;
     split_rate(st->A, a_hi, a_lo);
-    KahanF32 s0;
-    float s0c = 0.f, s1 = 0.f, s2 = 0.f;
-    stream_f32(tau, n, [&](long long, float t) {
-        float e, c;
-        exp_neg(t, a_hi, a_lo, e, c);
-        s0.add(e);
-        s0c += c;
-        const float te = t * e;
-        s1 += te;
-        s2 = fmaf(t, te, s2);
-    });
     __shared__ double sh[4][32];
-    double v[4] = {(double)s0.value(), (double)s0c, (double)s1, (double)s2};
+    double v[4];
+    if constexpr (PRECISE) {
+        DFSum s0;
+        KahanF32 s1;                                  // g' enters the step's certificate
+        float s2 = 0.f;
+        stream_f32(tau, n, [&](long long, float t) {
+            float eh, el;
+            exp2_neg_precise(t, a_hi, a_lo, tab, eh, el);
+            s0.add(eh, el);
+            const float te = t * eh;
+            s1.add(te);
+            s2 = fmaf(t, te, s2);
+        });
+        v[0] = s0.value();
+        v[1] = 0.0;
+        v[2] = (double)s1.s - (double)s1.c;
+        v[3] = (double)s2;
+    } else {
+        KahanF32 s0;
+        float s0c = 0.f, s1 = 0.f, s2 = 0.f;
+        stream_f32(tau, n, [&](long long, float t) {
+            float e, c;
+            exp_neg(t, a_hi, a_lo, e, c);
+            s0.add(e);
+            s0c += c;
+            const float te = t * e;
+            s1 += te;
+            s2 = fmaf(t, te, s2);
+        });
+        v[0] = (double)s0.value();
+        v[1] = (double)s0c;
+        v[2] = (double)s1;
+        v[3] = (double)s2;
+    }
     block_sum<4>(v, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = Partial{v[0], v[1], v[2], v[3], 0, 0};
     if (!last_block(&st->ticket)) return;
@@ -160,7 +194,7 @@ __global__ void __launch_bounds__(kThreads) mf_newton_kernel(const float* __rest
     partial_totals<4>(part, gridDim.x, tot, sh, [](const Partial& p, double (&x)[4]) {
         x[0] = p.s0; x[1] = p.s0c; x[2] = p.s1; x[3] = p.s2;
     });
-    if (threadIdx.x == 0) halley_update(st, tot[0], tot[1], tot[2], tot[3]);
+    if (threadIdx.x == 0) halley_update(st, tot[0], tot[1], tot[2], tot[3], PRECISE);
 }
 
 // ---- F = exp(-A tau), the convergence check at that A and, optionally, the
@@ -184,6 +218,8 @@ __global__ void __launch_bounds__(kThreads) mf_flux_kernel(const float* __restri
         for (int k = 0; k < 21; ++k) mine[k] = 0;
     float a_hi, a_lo;
     split_rate(st->A, a_hi, a_lo);
+    // F in FP32 (MUFU exponential, first-order argument correction); the sum
+    // of e only cross-checks the precise pass's decision
     KahanF32 s0, m1, m2;
     float s0c = 0.f;
     auto proc = [&](float t) {
@@ -453,9 +489,9 @@ cudaError_t launch_field_check(const float* rho, const float* vpec, const float*
 namespace {
 
 // The host side of one root-find on caller-chosen scratch: the init pass,
-// then rounds of two Halley passes and one flux pass (which writes F, if
-// asked, and checks |g| <= tol at the final A), reading the state back once
-// per round.
+// then rounds of two Halley passes (MUFU, then precise: the latter decides
+// convergence) and one flux pass (which writes F, if asked, at the final A),
+// reading the state back once per round.
 static lya_status solve_on_scratch(const float* tau, int64_t n, double target, double tol, int max_iter,
                                    double* A_out, float* flux_out, MFState* st, Partial* part, int grid,
                                    cudaStream_t stream, StatPart* spart = nullptr, StatsOut* sout = nullptr,
@@ -477,8 +513,12 @@ static lya_status solve_on_scratch(const float* tau, int64_t n, double target, d
         err = cudaGetLastError();
     }
     for (int round = 0; err == cudaSuccess; ++round) {
-        for (int b = 0; b < 2 && err == cudaSuccess; ++b) {
-            mf_newton_kernel<<<grid, kThreads, 0, stream>>>(tau, n, st, part);
+        // a fast (MUFU) Halley pass, a precise one, then the flux pass
+        mf_newton_kernel<false><<<grid, kThreads, 0, stream>>>(tau, n, st, part);
+        count_launch();
+        err = cudaGetLastError();
+        if (err == cudaSuccess) {
+            mf_newton_kernel<true><<<grid, kThreads, 0, stream>>>(tau, n, st, part);
             count_launch();
             err = cudaGetLastError();
         }
@@ -692,21 +732,23 @@ __global__ void __launch_bounds__(kThreads) mf_moments_kernel(const float* __res
 __global__ void __launch_bounds__(kThreads) mf_sums_kernel(const float* __restrict__ tau, long long n, double A,
                                                          Partial* part, SumsOut* out)
 {
+    __shared__ float2 tab[kExp2TabSize];
+    load_exp2_table(tab);
     float a_hi, a_lo;
     split_rate(A, a_hi, a_lo);
-    KahanF32 s0;
-    float s0c = 0.f, s1 = 0.f, s2 = 0.f;
+    DFSum s0;                                   // sum e precise (double-float exponentials)
+    KahanF32 s1;
+    float s2 = 0.f;
     stream_f32(tau, n, [&](long long, float t) {
-        float e, c;
-        exp_neg(t, a_hi, a_lo, e, c);
-        s0.add(e);
-        s0c += c;
-        const float te = t * e;
-        s1 += te;
+        float eh, el;
+        exp2_neg_precise(t, a_hi, a_lo, tab, eh, el);
+        s0.add(eh, el);
+        const float te = t * eh;
+        s1.add(te);
         s2 = fmaf(t, te, s2);
     });
     __shared__ double sh[4][32];
-    double v[4] = {(double)s0.value(), (double)s0c, (double)s1, (double)s2};
+    double v[4] = {s0.value(), 0.0, (double)s1.s - (double)s1.c, (double)s2};
     block_sum<4>(v, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = Partial{v[0], v[1], v[2], v[3], 0, 0};
     if (!last_block(&out->ticket)) return;
@@ -779,6 +821,82 @@ lya_status flux_at_run(const float* tau, int64_t n, double A, float* flux, cudaS
     mf_flux_at_kernel<<<grid_for(n), kThreads, 0, stream>>>(tau, n, A, flux);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? LYA_OK : LYA_ECUDA;
+}
+
+// ---- the split root-find stepped on the host --------------------------------------
+namespace {
+MFIter to_core(const lya_mean_flux_iter& it)
+{
+    return MFIter{it.A, it.lo, it.hi, it.g, it.iter, it.max_iter, it.done, (int)it.status};
+}
+void from_core(lya_mean_flux_iter& it, const MFIter& c)
+{
+    it.A = c.A;
+    it.lo = c.lo;
+    it.hi = c.hi;
+    it.g = c.g;
+    it.iter = c.iter;
+    it.max_iter = c.max_iter;
+    it.done = c.done;
+    it.status = (lya_status)c.status;
+}
+}  // namespace
+
+lya_status mean_flux_start(const double totals[4], double target, double tol, int max_iter, lya_mean_flux_iter* it)
+{
+    *it = lya_mean_flux_iter{};
+    it->target = target;
+    it->tol = tol;
+    it->n = totals[3];
+    it->max_iter = max_iter;
+    MFIter c = to_core(*it);
+    mf_start(c, target, totals[3], totals[0], totals[1], totals[2]);
+    from_core(*it, c);
+    return it->done ? it->status : LYA_OK;
+}
+
+lya_status mean_flux_step(lya_mean_flux_iter* it, const double sums[3])
+{
+    if (it->done) return it->status;
+    MFIter c = to_core(*it);
+    // the shares' sum of e is precise (lya_mean_flux_sums): every step may end
+    // the iteration; tau_max is not summed over parts, so only steps from below
+    // the root (dA > 0, the Newton iteration's side) are certified
+    mf_step(c, sums[0] / it->n - it->target, -sums[1] / it->n, sums[2] / it->n, it->tol, INFINITY, true);
+    from_core(*it, c);
+    return it->done ? it->status : LYA_OK;
+}
+
+lya_status mean_flux_sharded(const float* tau, int64_t n, double target, double tol, int max_iter,
+                             lya_allreduce_fn allreduce, void* user, double* A_out, int* iters_out, float* flux_out,
+                             cudaStream_t stream)
+{
+    double tot[4] = {0.0, 0.0, 0.0, (double)n};
+    if (n > 0) {
+        const lya_status st = tau_moments_run(tau, n, tot, stream);
+        if (st != LYA_OK) return st;
+    }
+    if (allreduce(tot, 4, user) != 0) return LYA_ECUDA;
+    if (!(tot[3] > 0.0)) return LYA_EINVAL;
+    lya_mean_flux_iter it;
+    lya_status st = mean_flux_start(tot, target, tol, max_iter, &it);
+    while (st == LYA_OK && !it.done) {
+        double sums[3] = {0.0, 0.0, 0.0};
+        if (n > 0) {
+            st = mean_flux_sums_run(tau, n, it.A, sums, stream);
+            if (st != LYA_OK) return st;
+        }
+        if (allreduce(sums, 3, user) != 0) return LYA_ECUDA;
+        st = mean_flux_step(&it, sums);
+    }
+    if (st != LYA_OK) return st;
+    *A_out = it.A;
+    if (iters_out) *iters_out = it.iter;
+    if (flux_out && n > 0) {
+        st = flux_at_run(tau, n, it.A, flux_out, stream);
+        if (st == LYA_OK && cudaStreamSynchronize(stream) != cudaSuccess) st = LYA_ECUDA;
+    }
+    return st;
 }
 
 }  // namespace lya

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdint>
 
+#include "exp2_table.h"
 #include "lya_device.cuh"
 #include "lya_internal.h"
 
@@ -67,6 +68,7 @@ struct MFState {
     long long n, n_zero, n_bad;
     int iter, max_iter, done, status;   // status: LYA_OK / LYA_EINVAL / LYA_ENOCONV (not yet converged)
     unsigned int ticket;
+    unsigned int tau_max_bits;          // largest tau (float bits; tau >= 0 orders like its bits)
     unsigned long long hist[kHistBins + 1];   // + sampled zeros
 };
 
@@ -189,6 +191,80 @@ __device__ __forceinline__ void exp_neg(float t, float a_hi, float a_lo, float& 
     corr = -e * y_lo * kLn2f;
 }
 
+// ---- precise passes: e = 2^-y to ~1e-15 relative on the FP32 pipe -----------------
+// GB300 runs FP64 at a small fraction of its FP32 rate, so a per-pixel FP64
+// exponential would cost milliseconds per pass over 2.7e8 pixels; instead the
+// exponential is formed in double-float arithmetic (pairs of floats) from the
+// split y = t (a_hi + a_lo) = y_hi + y_lo (exact to ~2^-48 y):
+//   y_hi = N/1024 + r,  N = rint(1024 y_hi),  |r| <= 2^-11 (r exact),
+//   2^-y = 2^-(N >> 10) * 2^(-(N & 1023)/1024) * exp(u),  u = -(r + y_lo) ln 2,
+// the middle factor a double-float from kExp2Tab (in shared memory), exp(u) =
+// 1 + u + u^2/2 + u^3/6 with |u| <= 3.4e-4 (the next term is below 6e-16),
+// u itself a double-float (ln 2 split into two floats).  Values with
+// y >= 125 (e < 3e-38) are returned as 0.  Result: e_hi + e_lo.
+constexpr float kLn2Hi = 0x1.62e430p-1f;                 // float nearest ln 2
+constexpr float kLn2Lo = -0x1.05c610p-29f;               // ln 2 - kLn2Hi, to float
+
+// Copies kExp2Tab into shared memory (whole block; ends with a barrier).
+__device__ __forceinline__ void load_exp2_table(float2* tab)
+{
+    for (int k = threadIdx.x; k < kExp2TabSize; k += blockDim.x) tab[k] = kExp2Tab[k];
+    __syncthreads();
+}
+
+__device__ __forceinline__ void exp2_neg_precise(float t, float a_hi, float a_lo, const float2* __restrict__ tab,
+                                                 float& e_hi, float& e_lo)
+{
+    const float y_hi = t * a_hi;
+    const float y_lo = fmaf(t, a_lo, fmaf(t, a_hi, -y_hi));
+    if (!(y_hi < 125.f)) {
+        e_hi = 0.f;
+        e_lo = 0.f;
+        return;
+    }
+    const float Nf = rintf(y_hi * 1024.f);
+    const int N = (int)Nf;
+    const float r = fmaf(Nf, -1.f / 1024.f, y_hi);                     // exact
+    const float u_hi = -r * kLn2Hi;
+    const float u_lo = fmaf(-r, kLn2Hi, -u_hi) - fmaf(r, kLn2Lo, y_lo * kLn2Hi);
+    // exp(u) - 1 = u_hi + d_lo, d_lo = u_lo + u_hi u_lo + u_hi^2/2 + u_hi^3/6
+    const float d_lo = fmaf(u_hi, fmaf(u_hi, fmaf(u_hi, 1.f / 6.f, 0.5f), u_lo), u_lo);
+    const float2 T = tab[N & (kExp2TabSize - 1)];
+    // T (1 + u_hi + d_lo) with the product T.x u_hi exact (two-product)
+    const float P = T.x * u_hi;
+    const float Pe = fmaf(T.x, u_hi, -P);
+    const float R_hi = T.x + P;
+    float R_lo = (T.x - R_hi) + P;                                      // |T.x| > |P|: exact
+    R_lo += Pe + fmaf(T.x, d_lo, fmaf(T.y, u_hi, T.y));
+    const float scale = __int_as_float((127 - (N >> 10)) << 23);        // 2^-(N >> 10), exact
+    e_hi = R_hi * scale;
+    e_lo = R_lo * scale;
+}
+
+// Per-thread sum of e_hi + e_lo values: a float pair updated with an exact
+// two-sum, moved into an FP64 total every 32 terms so the pair's rounding
+// never builds up.
+struct DFSum {
+    double acc = 0.0;
+    float h = 0.f, l = 0.f;
+    int k = 0;
+    __device__ __forceinline__ void add(float eh, float el)
+    {
+        const float s = __fadd_rn(h, eh);
+        const float bp = __fsub_rn(s, h);
+        const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(eh, bp));
+        l = __fadd_rn(l, __fadd_rn(err, el));
+        h = s;
+        if (++k == 32) {
+            acc += (double)h + (double)l;
+            h = 0.f;
+            l = 0.f;
+            k = 0;
+        }
+    }
+    __device__ __forceinline__ double value() const { return acc + ((double)h + (double)l); }
+};
+
 // Sec. 5.2 bin: k with (2k-1)/40 <= F < (2k+1)/40, clamped to [0, 20].  The
 // guess floor(20 F + 1/2) is off by at most one; fma(F, 40, -(2k +- 1)) is
 // the exact difference rounded once, so its sign decides the edge exactly.
@@ -255,83 +331,174 @@ __device__ inline void proxy_start(MFState* st)
 }
 
 // ---- the steps on the reduced sums (one thread) --------------------------------
+// The iteration's state and steps are shared by the device passes (the
+// single-request and batched root-finds) and the host driver of a root-find
+// whose pixels are split over several devices (lya_mean_flux_step).
 
-// After the init pass: record <tau> and the zero/invalid counts; fail on an
-// invalid value or when no A can reach F_t (the zero-tau pixels alone give
-// <F> >= F_t); else start from the Jensen bound A0 = -ln(F_t)/<tau>, which is
-// below the root.  Returns true when the iteration goes on.
-__device__ inline bool init_finish(MFState* st, double sum_tau, long long zeros, long long bad)
+// Bound on the error of g(A) from an FP32 (MUFU) pass: its steps move A but
+// never tighten the bracket with a sign that close to the root, and never end
+// the iteration; only a precise pass (g to ~1e-13) decides convergence.
+constexpr double kApproxGErr = 1e-6;
+// Bounds used by the precise pass's certificate: on the error of its g
+// (double-float exponentials, ~1e-15 per term, float-pair partial sums of 32
+// terms, FP64 beyond) and on the relative error of its g' (compensated FP32
+// per thread, FP64 beyond).
+constexpr double kPreciseGErr = 1e-13;
+constexpr double kSlopeRelErr = 1e-5;
+
+__host__ __device__ inline bool finite_d(double x) { return x == x && x - x == 0.0; }
+
+// The iteration: A in the bracket [lo, hi], the last g (or, once a step is
+// certified, the bound on |g| at the final A), passes taken, and whether it
+// has ended (status LYA_OK, or an error).
+struct MFIter {
+    double A, lo, hi, g;
+    int iter, max_iter, done, status;
+};
+
+// The start from the totals over all pixels: <tau> and the zero/invalid
+// counts; fail on an invalid value or when no A can reach F_t (the zero-tau
+// pixels alone give <F> >= F_t); else Newton's start A0 = -ln(F_t)/<tau>, the
+// Jensen bound, which lies below the root.  Returns true when the iteration
+// goes on.
+__host__ __device__ inline bool mf_start(MFIter& it, double Ft, double n, double sum_tau, double zeros, double bad)
 {
-    const long long n = st->n;
-    st->ticket = 0;
-    st->n_zero = zeros;
-    st->n_bad = bad;
-    st->mean_tau = sum_tau / (double)n;
-    st->iter = 0;
-    if (bad > 0 || !(st->mean_tau > 0.0)) {
-        st->status = LYA_EINVAL;
-        st->done = 1;
+    const double mean_tau = sum_tau / n;
+    it.iter = 0;
+    it.g = 0.0;
+    if (bad > 0.0 || !(mean_tau > 0.0)) {
+        it.status = LYA_EINVAL;
+        it.done = 1;
         return false;
     }
-    if ((double)zeros / (double)n >= st->Ft) {       // <e^{-A tau}> >= zero fraction for all A
-        st->status = LYA_ENOCONV;
-        st->done = 1;
+    if (zeros / n >= Ft) {                            // <e^{-A tau}> >= zero fraction for all A
+        it.status = LYA_ENOCONV;
+        it.done = 1;
         return false;
     }
-    st->A = -log(st->Ft) / st->mean_tau;
-    st->lo = st->A;
-    st->hi = INFINITY;
-    st->status = LYA_ENOCONV;                         // until converged
-    st->done = 0;
+    it.A = -log(Ft) / mean_tau;
+    it.lo = it.A;
+    it.hi = INFINITY;
+    it.status = LYA_ENOCONV;                          // until converged
+    it.done = 0;
     return true;
 }
 
-// One safeguarded step from the sums S0 + S0c = sum e, S1 = sum tau e,
-// S2 = sum tau^2 e at the current A: Halley's step, else Newton's, else
-// bisection, whichever stays inside the bracket [lo, hi].
-__device__ inline void halley_update(MFState* st, double S0, double S0c, double S1, double S2)
+// One safeguarded step from the means at the current A of e (g = <e> - F_t),
+// tau e (g' = -<tau e>) and tau^2 e (g'' = <tau^2 e>): Halley's step, else
+// Newton's, else bisection, whichever stays inside the bracket [lo, hi].
+// precise: g comes from a precise pass (else the FP32 approximation).
+//
+// A precise step ends the iteration when |g| <= tol at A, or when it can
+// certify its Newton step: with dA = -g/g', Taylor's theorem gives
+//   g(A + dA) = g''(xi) dA^2 / 2,  xi between A and A + dA,
+// and g''(x) = <tau^2 e^{-x tau}> is decreasing, so g''(xi) <= g''(A) when
+// dA > 0 and g''(xi) <= g''(A) e^{|dA| tau_max} when dA < 0; hence
+//   |g(A + dA)| <= g''(A) dA^2 f / 2 + kPreciseGErr + |g| kSlopeRelErr
+// (f = 1 or e^{|dA| tau_max}; the last two terms the errors of g and g'),
+// and a bound <= tol makes A + dA final without evaluating g there again.
+// tau_max = INFINITY when unknown (then only steps with dA > 0 certify).
+__host__ __device__ inline void mf_step(MFIter& it, double g, double g1, double g2, double tol, double tau_max,
+                                        bool precise)
 {
-    st->ticket = 0;
-    const double nn = (double)st->n;
-    const double g = (S0 + S0c) / nn - st->Ft;
-    const double g1 = -S1 / nn, g2 = S2 / nn;
-    const double A = st->A;
-    st->g = g;
-    st->iter += 1;
-    if (fabs(g) <= st->tol) {
-        st->status = LYA_OK;
-        st->done = 1;
+    const double A = it.A;
+    it.g = g;
+    it.iter += 1;
+    if (precise && fabs(g) <= tol) {
+        it.status = LYA_OK;
+        it.done = 1;
         return;
     }
-    if (g > 0.0) st->lo = A; else st->hi = A;
+    if (precise || fabs(g) > kApproxGErr) {
+        if (g > 0.0) it.lo = A; else it.hi = A;
+    }
+    if (precise && g1 < 0.0) {
+        const double dA = -g / g1;
+        const double An = A + dA;
+        const double f = dA >= 0.0 ? 1.0 : exp(-dA * tau_max);
+        const double bound = 0.5 * g2 * dA * dA * f + kPreciseGErr + fabs(g) * kSlopeRelErr;
+        if (An > it.lo && An < it.hi && bound <= tol) {
+            it.A = An;
+            it.g = bound;                             // the certified bound on |g| at the final A
+            it.status = LYA_OK;
+            it.done = 1;
+            return;
+        }
+    }
     const double den = 2.0 * g1 * g1 - g * g2;
     double An = den > 0.0 ? A - 2.0 * g * g1 / den : NAN;
-    if (!isfinite(An) || An <= st->lo || An >= st->hi) An = g1 < 0.0 ? A - g / g1 : NAN;
-    if (!isfinite(An) || An <= st->lo || An >= st->hi)
-        An = isfinite(st->hi) ? 0.5 * (st->lo + st->hi) : 2.0 * st->lo;
-    if (fabs(An - A) <= 4.0e-16 * fabs(A)) {        // stalled at FP64 resolution
-        st->status = LYA_OK;
-        st->done = 1;
+    if (!finite_d(An) || An <= it.lo || An >= it.hi) An = g1 < 0.0 ? A - g / g1 : NAN;
+    if (!finite_d(An) || An <= it.lo || An >= it.hi) An = finite_d(it.hi) ? 0.5 * (it.lo + it.hi) : 2.0 * it.lo;
+    if (fabs(An - A) <= 4.0e-16 * fabs(A)) {          // stalled at FP64 resolution
+        if (precise) {
+            it.status = LYA_OK;
+            it.done = 1;
+        }
         return;
     }
-    st->A = An;
-    if (st->iter >= st->max_iter) {
-        st->status = LYA_ENOCONV;
-        st->done = 1;
+    it.A = An;
+    if (it.iter >= it.max_iter) {
+        it.status = LYA_ENOCONV;
+        it.done = 1;
     }
 }
 
-// The check of the flux pass: the F just written is final when |g| <= tol at
-// this A (or the iteration had already stopped at FP64 resolution).
+__device__ inline MFIter iter_of(const MFState* st)
+{
+    return MFIter{st->A, st->lo, st->hi, st->g, st->iter, st->max_iter, st->done, st->status};
+}
+__device__ inline void set_iter(MFState* st, const MFIter& it)
+{
+    st->A = it.A;
+    st->lo = it.lo;
+    st->hi = it.hi;
+    st->g = it.g;
+    st->iter = it.iter;
+    st->max_iter = it.max_iter;
+    st->done = it.done;
+    st->status = it.status;
+}
+
+// After the init pass (device): record <tau> and the counts, and start.
+__device__ inline bool init_finish(MFState* st, double sum_tau, long long zeros, long long bad)
+{
+    st->ticket = 0;
+    st->n_zero = zeros;
+    st->n_bad = bad;
+    st->mean_tau = sum_tau / (double)st->n;
+    MFIter it = iter_of(st);
+    const bool go = mf_start(it, st->Ft, (double)st->n, sum_tau, (double)zeros, (double)bad);
+    set_iter(st, it);
+    return go;
+}
+
+// A Halley pass's step from its sums S0 + S0c = sum e, S1 = sum tau e,
+// S2 = sum tau^2 e (device).
+__device__ inline void halley_update(MFState* st, double S0, double S0c, double S1, double S2, bool precise)
+{
+    st->ticket = 0;
+    const double nn = (double)st->n;
+    MFIter it = iter_of(st);
+    mf_step(it, (S0 + S0c) / nn - st->Ft, -S1 / nn, S2 / nn, st->tol, (double)__uint_as_float(st->tau_max_bits),
+            precise);
+    set_iter(st, it);
+}
+
+// After the flux pass: the F just written is final when a precise pass has
+// ended the iteration at this A (|g| <= tol, a certified step, or a step
+// below FP64 resolution); else more passes are needed.  The pass's own FP32
+// g is only a consistency check of that decision.
 __device__ inline void flux_update(MFState* st, double S0, double S0c)
 {
     st->ticket = 0;
     const double g = (S0 + S0c) / (double)st->n - st->Ft;
-    st->g = g;
-    if (fabs(g) <= st->tol || (st->done && st->status == LYA_OK)) {
-        st->status = LYA_OK;
-        st->done = 1;
+    if (st->done && st->status == LYA_OK) {
+        if (!(fabs(g) <= kApproxGErr)) {             // cannot happen unless the sums are wrong
+            st->status = LYA_ENOCONV;
+            st->done = 0;
+        }
     } else {
+        st->g = g;
         st->status = LYA_ENOCONV;                     // more passes needed
         st->done = 0;
     }

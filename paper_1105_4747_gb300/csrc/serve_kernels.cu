@@ -7,8 +7,9 @@
 // to arrive (an atomic ticket in the request's state, no waiting) sums that
 // request's partials in FP64 and takes the same step as the single-request
 // kernels: init (the Jensen start refined by the histogram proxy), Halley
-// passes, and the flux pass that writes F = exp(-A tau), checks |g| <= tol at
-// that A and, when it holds, the request's flux statistics (Sec. 2.3, 5.2).
+// passes (MUFU, then precise: the latter decides convergence), and the flux
+// pass that writes F = exp(-A tau) and, once the root-find has ended, the
+// request's flux statistics (Sec. 2.3, 5.2).
 // Requests whose root-find has ended skip every later pass of the step.
 #include <cstdint>
 
@@ -67,6 +68,7 @@ __global__ void __launch_bounds__(kRfThreads) rf_reset_kernel(const unsigned cha
             st->done = 0;
             st->status = LYA_ENOCONV;
             st->ticket = 0;
+            st->tau_max_bits = 0u;
             SlotResult* res = results + s.state;
             res->final = 0;
             res->done = 0;
@@ -93,14 +95,18 @@ __global__ void __launch_bounds__(kRfThreads) rf_init_kernel(const unsigned char
         while ((s.n >> 22) > smask) smask = 2 * smask + 1;
         KahanF32 acc;
         long long z = 0, bad = 0;
+        float tmax = 0.f;
         stream_f32(s.tau + U.begin, U.end - U.begin, threadIdx.x, blockDim.x, [&](long long i, float t) {
             if (!(t >= 0.f) || !isfinite(t)) { ++bad; return; }
             acc.add(t);
             z += (t == 0.f);
+            tmax = fmaxf(tmax, t);
             if (((U.begin + i) & smask) == 0) atomicAdd(&h_s[t == 0.f ? kHistBins : hist_bin(t)], 1u);
         });
         double x[3] = {(double)acc.value(), (double)z, (double)bad};
         block_sum<3>(x, sh);
+        for (int o = 16; o > 0; o >>= 1) tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(&st->tau_max_bits, __float_as_uint(tmax));
         for (int b = threadIdx.x; b <= kHistBins; b += blockDim.x)
             if (h_s[b]) atomicAdd(&st->hist[b], (unsigned long long)h_s[b]);
         if (threadIdx.x == 0) part[u] = Partial{x[0], 0.0, 0.0, 0.0, (long long)x[1], (long long)x[2]};
@@ -119,7 +125,9 @@ __global__ void __launch_bounds__(kRfThreads) rf_init_kernel(const unsigned char
     }
 }
 
-// One Halley pass over every request still iterating.
+// One Halley pass over every request still iterating (PRECISE: the sum of e
+// in double-float, which may end a request's iteration; else the MUFU form).
+template <bool PRECISE>
 __global__ void __launch_bounds__(kRfThreads) rf_halley_kernel(const unsigned char* __restrict__ step,
                                                              MFState* states, SlotResult* results, Partial* part)
 {
@@ -127,6 +135,8 @@ __global__ void __launch_bounds__(kRfThreads) rf_halley_kernel(const unsigned ch
     __shared__ double sh[4][32];
     __shared__ int s_skip;
     __shared__ double s_A;
+    __shared__ float2 tab[PRECISE ? kExp2TabSize : 1];
+    if constexpr (PRECISE) load_exp2_table(tab);
     for (int u = blockIdx.x; u < v.hdr->n_units; u += gridDim.x) {
         const RfUnit U = v.units[u];
         const RfSlot s = v.rf[U.rf];
@@ -142,18 +152,40 @@ __global__ void __launch_bounds__(kRfThreads) rf_halley_kernel(const unsigned ch
         }
         float a_hi, a_lo;
         split_rate(s_A, a_hi, a_lo);
-        KahanF32 s0;
-        float s0c = 0.f, s1 = 0.f, s2 = 0.f;
-        stream_f32(s.tau + U.begin, U.end - U.begin, threadIdx.x, blockDim.x, [&](long long, float t) {
-            float e, c;
-            exp_neg(t, a_hi, a_lo, e, c);
-            s0.add(e);
-            s0c += c;
-            const float te = t * e;
-            s1 += te;
-            s2 = fmaf(t, te, s2);
-        });
-        double x[4] = {(double)s0.value(), (double)s0c, (double)s1, (double)s2};
+        double x[4];
+        if constexpr (PRECISE) {
+            DFSum s0;
+            KahanF32 s1;                              // g' enters the step's certificate
+            float s2 = 0.f;
+            stream_f32(s.tau + U.begin, U.end - U.begin, threadIdx.x, blockDim.x, [&](long long, float t) {
+                float eh, el;
+                exp2_neg_precise(t, a_hi, a_lo, tab, eh, el);
+                s0.add(eh, el);
+                const float te = t * eh;
+                s1.add(te);
+                s2 = fmaf(t, te, s2);
+            });
+            x[0] = s0.value();
+            x[1] = 0.0;
+            x[2] = (double)s1.s - (double)s1.c;
+            x[3] = (double)s2;
+        } else {
+            KahanF32 s0;
+            float s0c = 0.f, s1 = 0.f, s2 = 0.f;
+            stream_f32(s.tau + U.begin, U.end - U.begin, threadIdx.x, blockDim.x, [&](long long, float t) {
+                float e, c;
+                exp_neg(t, a_hi, a_lo, e, c);
+                s0.add(e);
+                s0c += c;
+                const float te = t * e;
+                s1 += te;
+                s2 = fmaf(t, te, s2);
+            });
+            x[0] = (double)s0.value();
+            x[1] = (double)s0c;
+            x[2] = (double)s1;
+            x[3] = (double)s2;
+        }
         block_sum<4>(x, sh);
         if (threadIdx.x == 0) part[u] = Partial{x[0], x[1], x[2], x[3], 0, 0};
         if (!last_arrival(&st->ticket, (unsigned)s.unit_count)) continue;
@@ -162,7 +194,7 @@ __global__ void __launch_bounds__(kRfThreads) rf_halley_kernel(const unsigned ch
             y[0] = p.s0; y[1] = p.s0c; y[2] = p.s1; y[3] = p.s2;
         });
         if (threadIdx.x == 0) {
-            halley_update(st, tot[0], tot[1], tot[2], tot[3]);
+            halley_update(st, tot[0], tot[1], tot[2], tot[3], PRECISE);
             if (st->done && st->status != LYA_OK) publish(st, results + s.state, true);
         }
         __syncthreads();
@@ -187,7 +219,8 @@ __global__ void __launch_bounds__(kRfThreads) rf_flux_kernel(const unsigned char
         const RfSlot s = v.rf[U.rf];
         MFState* st = states + s.state;
         if (threadIdx.x == 0) {
-            s_skip = st->done && st->status != LYA_OK;      // an error is final
+            // an error is final, and so is an F already written this step
+            s_skip = (st->done && st->status != LYA_OK) || results[s.state].final;
             s_A = st->A;
         }
         __syncthreads();
@@ -277,8 +310,8 @@ cudaError_t serve_rf_launch(const unsigned char* d_step, void* d_states, SlotRes
     rf_init_kernel<<<grid, kRfThreads, 0, stream>>>(d_step, st, d_results, part);
     ++n;
     for (int r = 0; r < kRfRounds; ++r) {
-        rf_halley_kernel<<<grid, kRfThreads, 0, stream>>>(d_step, st, d_results, part);
-        rf_halley_kernel<<<grid, kRfThreads, 0, stream>>>(d_step, st, d_results, part);
+        rf_halley_kernel<false><<<grid, kRfThreads, 0, stream>>>(d_step, st, d_results, part);
+        rf_halley_kernel<true><<<grid, kRfThreads, 0, stream>>>(d_step, st, d_results, part);
         rf_flux_kernel<<<grid, kRfThreads, 0, stream>>>(d_step, st, d_results, part, sp);
         n += 3;
     }

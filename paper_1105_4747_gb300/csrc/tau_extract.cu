@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <cfloat>
 #include <cstdint>
+#include <cstdlib>
 #include <mutex>
 
 #include "lya_device.cuh"
@@ -91,7 +92,10 @@ __device__ __forceinline__ int wrap_pixel(int x, int N)
 }
 
 // ---- per-source preparation -------------------------------------------------
-struct SrcF32 { float a, bb, w; int t, h; };
+// lw = log2 of the source's weight rho^2 (T/1e4)^-0.7 / (T/1e4)^0.5 (n_HI / b
+// of Eq. 4 and 6 up to the constant K): the pair term w 2^-x^2 is then one
+// exponential 2^(lw - x^2), its argument one FFMA.
+struct SrcF32 { float a, bb, lw; int t, h; };
 
 __device__ __forceinline__ float target_shift_f32(float v, const TauLaunch& L)
 {
@@ -101,9 +105,10 @@ __device__ __forceinline__ float target_shift_f32(float v, const TauLaunch& L)
 __device__ __forceinline__ SrcF32 prep_f32(const TauLaunch& L, float rho, float v, float T, int j)
 {
     SrcF32 s;
-    if (L.t_mode != 0) T = L.T0 * ex2(L.gm1 * lg2(fminf(rho, L.pivot)));
-    const float lt = lg2(T) - kLog2_1e4;                 // log2(T / 1e4 K)
-    s.w = rho * rho * ex2(-1.2f * lt);                   // rho^2 (T/1e4)^-0.7 / (T/1e4)^0.5
+    const float lr = lg2(rho);                           // log2 rho
+    // log2(T / 1e4 K): stored, or Eq. 5 in log form, T0 min(rho, pivot)^(gamma-1)
+    const float lt = L.t_mode != 0 ? fmaf(L.gm1, fminf(lr, L.lpivot), L.lT0) : lg2(T) - kLog2_1e4;
+    s.lw = fmaf(-1.2f, lt, 2.f * lr);
     const float c = L.c_coef * ex2(-0.5f * lt);          // sqrt(log2 e) / b
     const float sf = target_shift_f32(v, L);
     float r = fmaf(-sf, L.du_hi, v);                     // exact product inside the fma
@@ -225,7 +230,7 @@ __global__ void __launch_bounds__(512) tau_kernel(const TauLaunch L)
             const SrcF32 s = prep_f32(L, r, v, T, j);
             const int pos = atomicAdd(&bin[s.t + 1], 1);
             if (pos >= N) { atomicOr(L.err, 2); continue; }   // input changed under the kernel
-            rec[pos] = make_float4(s.a, s.bb, s.w, (float)j);
+            rec[pos] = make_float4(s.a, s.bb, ex2(s.lw), (float)j);
             hmax = max(hmax, s.h);
         }
     }
@@ -326,6 +331,7 @@ constexpr float kHalfSqrtPi = 0.88622692545275801f;
 __host__ __device__ __forceinline__ int round_up4(int n) { return (n + 3) & ~3; }
 
 constexpr int kLocalReach = 64;                  // window bound up to which tiles search their runs locally
+constexpr unsigned kStageSpins = 1u << 22;       // polls of the staged inputs' mbarrier before giving up
 
 // Records past the seam copied to the ends of the record array (local
 // searches only), so that every tile's candidates are one contiguous run:
@@ -457,7 +463,8 @@ __device__ __forceinline__ float cell_erf(float y, float hw)
 }
 
 // Two adjacent pixels fo, fo + 1 (in the run's frame) against candidates [k0, k1).
-// AVG: records hold the averaged-profile constants {du/b, r/b, w sqrt(pi) b/2du, t}.
+// Records {a, c r, lw, t} (sampled profile: term 2^(lw - x^2)); AVG: records
+// hold the averaged-profile constants {du/b, r/b, w sqrt(pi) b/2du, t}.
 template <bool COMP, bool AVG, int FOLD = 8>
 __device__ __forceinline__ void pair2_segment(const float4* __restrict__ rec, int k0, int k1, float fo,
                                               float (&S)[2], float (&C)[2])
@@ -470,8 +477,8 @@ __device__ __forceinline__ void pair2_segment(const float4* __restrict__ rec, in
             t0 = r.z * cell_erf(x0, hw);
             t1 = r.z * cell_erf(x1, hw);
         } else {
-            t0 = r.z * ex2(-(x0 * x0));
-            t1 = r.z * ex2(-(x1 * x1));
+            t0 = ex2(fmaf(-x0, x0, r.z));                             // r.z = lw
+            t1 = ex2(fmaf(-x1, x1, r.z));
         }
     };
     int k = k0;
@@ -593,13 +600,14 @@ constexpr float kRecMaxA = 0.5f;
 // Four adjacent pixels fo .. fo + 3 against candidates [k0, k1) (long runs:
 // a record read from shared memory serves four pixels).  EXP selects how the
 // four exponentials 2^-x_m^2, x_m = x_0 + m a, are formed:
-//   LYA_EXP_MUFU        four MUFU ex2;
+//   LYA_EXP_MUFU        four MUFU ex2 of lw - x_m^2 (records carry lw);
 //   LYA_EXP_RECURRENCE  the Gaussian recurrence of fast Gaussian gridding
 //                       (Greengard & Lee 2004): E_{m+1} = E_m Q_m,
 //                       Q_{m+1} = Q_m R with Q_0 = 2^-a(2 x_0 + a), R = 2^-2a^2:
 //                       three MUFU and two FMUL per further pixel (lines with
 //                       a <= kRecMaxA; wider pixels take the MUFU form);
 //   LYA_EXP_POLY_SPLIT  three MUFU and one exp2_poly on the FMA pipe.
+// (the last two take records with the linear weight w = 2^lw)
 template <bool COMP, bool AVG, int EXP>
 __device__ __forceinline__ void pair4_segment(const float4* __restrict__ rec, int k0, int k1, float fo,
                                               float (&S)[4], float (&C)[4])
@@ -627,6 +635,12 @@ __device__ __forceinline__ void pair4_segment(const float4* __restrict__ rec, in
                     const float x = fmaf((float)m, r.x, x0);
                     t[m] = r.z * ex2(-(x * x));
                 }
+            }
+        } else if constexpr (EXP == LYA_EXP_MUFU) {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const float x = fmaf((float)m, r.x, x0);
+                t[m] = ex2(fmaf(-x, x, r.z));                         // r.z = lw
             }
         } else {
 #pragma unroll
@@ -693,7 +707,7 @@ __device__ __forceinline__ void pair4_segment(const float4* __restrict__ rec, in
 // records [k0, k1) with targets in [0, N), at the periodic image nearest each
 // pixel (velocity difference in [-V/2, V/2), as Eq. 6 is read), NPX pixels
 // fo .. fo + NPX - 1.  Slow, and met only in such boxes.
-template <bool COMP, bool AVG, int NPX>
+template <bool COMP, bool AVG, int NPX, bool LOGW>
 __device__ __forceinline__ void wrap_segment(const float4* __restrict__ rec, int k0, int k1, float fo, float Nf,
                                           float (&S)[NPX], float (&C)[NPX])
 {
@@ -705,7 +719,8 @@ __device__ __forceinline__ void wrap_segment(const float4* __restrict__ rec, int
             float x = fmaf(mi, r.x, -r.y);
             if (x >= 0.5f * Nf * r.x) x = fmaf(mi - Nf, r.x, -r.y);
             else if (x < -0.5f * Nf * r.x) x = fmaf(mi + Nf, r.x, -r.y);
-            const float t = AVG ? r.z * cell_erf(x, 0.5f * r.x) : r.z * ex2(-(x * x));
+            const float t = AVG ? r.z * cell_erf(x, 0.5f * r.x)
+                                : (LOGW ? ex2(fmaf(-x, x, r.z)) : r.z * ex2(-(x * x)));
             if constexpr (COMP) kahan_fold(S[m], C[m], t);
             else S[m] += t;
         }
@@ -728,7 +743,7 @@ __device__ __forceinline__ void tiles_by_four(const float4* __restrict__ rec, co
         const int o = kTile * tile + 4 * half;
         float S[4] = {0.f, 0.f, 0.f, 0.f}, C[4] = {0.f, 0.f, 0.f, 0.f};
         if (ot & kWrapTile) {
-            wrap_segment<COMP, AVG, 4>(rec, base, base + nsrc, (float)o, (float)N, S, C);
+            wrap_segment<COMP, AVG, 4, !AVG && EXP == LYA_EXP_MUFU>(rec, base, base + nsrc, (float)o, (float)N, S, C);
         } else if (ext) {
             pair4_segment<COMP, AVG, EXP>(rec, ok0[i], ok1[i], (float)o, S, C);
         } else {
@@ -749,11 +764,15 @@ __device__ __forceinline__ void tiles_by_four(const float4* __restrict__ rec, co
 // group's own shared scratch.  N <= MAXQ * g.nt.
 // FOLD: candidates per Kahan fold in the two-pixel loop (8, or 4 where registers
 // are scarcer: the serving kernel and the four-sources-per-thread tile kernel).
-template <bool COMP, int MAXQ, bool AVG = false, bool ALT_EXP = false, int FOLD = 8>
+// STAGE: the skewer's inputs arrive by three 1D bulk copies (the TMA engine)
+// into the record area, issued by the group's first thread and counted on
+// the mbarrier *bar; needs N % 4 == 0 and 16-byte aligned rows.  Otherwise
+// every thread loads its sources with 16-byte (or scalar) loads.
+template <bool COMP, int MAXQ, bool AVG = false, bool ALT_EXP = false, int FOLD = 8, bool STAGE = false>
 __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __restrict__ rho,
                                             const float* __restrict__ vpec, const float* __restrict__ temp,
                                             float* out, unsigned char* smem, int* warp_tot, int* tile_hist,
-                                            const Group& g)
+                                            const Group& g, unsigned long long* bar = nullptr)
 {
     const int N = L.n_pix;
     const int Wd = L.w_max;
@@ -778,7 +797,19 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
     const int rec_cap = round_up4(N + Cx);                  // records the shared memory holds
     LYA_BOUND(N <= MAXQ * nt && NT <= kWrapTile);
     float r_[MAXQ], v_[MAXQ], T_[MAXQ];
-    if (vec) {
+    float* s_rho = reinterpret_cast<float*>(rec);           // staged inputs (STAGE), 12 N bytes
+    float* s_v = s_rho + N;
+    float* s_T = s_v + N;
+    if constexpr (STAGE) {
+        if (tid == 0) {
+            mbar_init(bar, 1);
+            const unsigned bytes = 4u * (unsigned)N;
+            mbar_expect_tx(bar, (temp ? 3u : 2u) * bytes);
+            bulk_copy_g2s(s_rho, rho, bytes, bar);
+            bulk_copy_g2s(s_v, vpec, bytes, bar);
+            if (temp) bulk_copy_g2s(s_T, temp, bytes, bar);
+        }
+    } else if (vec) {
 #pragma unroll
         for (int u4 = 0; u4 < MAXQ / 4; ++u4) {
             const int grp = tid + u4 * nt;
@@ -826,11 +857,34 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
         warp_tot[kRunTotal] = 0;
         warp_tot[kSkewerReach] = 0;
     }
-    g.sync();
+    g.sync();                       // (also: the mbarrier is initialised before anyone waits on it)
+    if constexpr (STAGE) {
+        if (!mbar_wait(bar, 0, kStageSpins)) {
+            // the copies did not land in time: flag it (bit 3) and wait once
+            // more, bounded, so none is still in flight when the CTA moves on
+            if ((tid & 31) == 0) atomicOr(L.err, 8);
+            mbar_wait(bar, 0, kStageSpins);
+        }
+#pragma unroll
+        for (int u4 = 0; u4 < MAXQ / 4; ++u4) {
+            const int grp = tid + u4 * nt;
+            if (4 * grp < N) {
+                const float4 a = reinterpret_cast<const float4*>(s_rho)[grp];
+                const float4 b = reinterpret_cast<const float4*>(s_v)[grp];
+                const float4 c = temp ? reinterpret_cast<const float4*>(s_T)[grp] : make_float4(0.f, 0.f, 0.f, 0.f);
+                r_[4 * u4] = a.x; r_[4 * u4 + 1] = a.y; r_[4 * u4 + 2] = a.z; r_[4 * u4 + 3] = a.w;
+                v_[4 * u4] = b.x; v_[4 * u4 + 1] = b.y; v_[4 * u4 + 2] = b.z; v_[4 * u4 + 3] = b.w;
+                T_[4 * u4] = c.x; T_[4 * u4 + 1] = c.y; T_[4 * u4 + 2] = c.z; T_[4 * u4 + 3] = c.w;
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) r_[4 * u4 + u] = 0.f;
+            }
+        }
+    }
 
     // 2. per-source constants (kept in registers) and the histogram of target
     //    pixels; th_ packs (target << 16) | reach, -1 = no source
-    float a_[MAXQ], bb_[MAXQ], w_[MAXQ];
+    float a_[MAXQ], bb_[MAXQ], w_[MAXQ];                 // w_: lw, or the linear weight (see below)
     int th_[MAXQ];
     int hsk = 0;
 #pragma unroll
@@ -844,12 +898,14 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
                 // w sqrt(pi) b / 2du; the window grows by the half cell
                 s.a *= kSqrtLn2;
                 s.bb *= kSqrtLn2;
-                s.w *= kHalfSqrtPi / s.a;
+                s.lw = ex2(s.lw) * (kHalfSqrtPi / s.a);
                 s.h = min(s.h + 1, L.w_max);
+            } else if (ALT_EXP && L.exp_method != LYA_EXP_MUFU) {
+                s.lw = ex2(s.lw);                    // the other exponential forms take w itself
             }
             a_[q] = s.a;
             bb_[q] = s.bb;
-            w_[q] = s.w;
+            w_[q] = s.lw;
             th_[q] = (s.t << 16) | s.h;
             LYA_BOUND(s.t >= 0 && s.t < N && s.h >= 0 && s.h <= Wd);
             atomicAdd(&cnt[s.t], 1);
@@ -1046,7 +1102,7 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
         LYA_BOUND(ext || (ot & kWrapTile) || Lt[tile] > Rt[tile] || (Lt[tile] >= -Wd && Rt[tile] < N + Wd));
         float S[2] = {0.f, 0.f}, C[2] = {0.f, 0.f};
         if (ot & kWrapTile) {
-            wrap_segment<COMP, AVG, 2>(rec, base, base + nsrc, (float)o, (float)N, S, C);
+            wrap_segment<COMP, AVG, 2, !AVG>(rec, base, base + nsrc, (float)o, (float)N, S, C);
         } else if (ext) {
             pair2_segment<COMP, AVG, FOLD>(rec, ok0[i], ok1[i], (float)o, S, C);
         } else {
@@ -1069,12 +1125,13 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
     }
 }
 
-template <bool COMP, int MAXQ, bool AVG, int NTB>
+template <bool COMP, int MAXQ, bool AVG, int NTB, bool STAGE>
 __global__ void __launch_bounds__(NTB, NTB >= 1024 ? 1 : 2) tau_tile_kernel(const TauLaunch L)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int warp_tot[kGroupScanInts];
     __shared__ __align__(16) int tile_hist[kTileKeys];
+    __shared__ __align__(8) unsigned long long stage_bar;
     const int64_t row = blockIdx.x;
     const int64_t sk = L.ids ? L.ids[row] : row;
     const int N = L.n_pix;
@@ -1097,9 +1154,9 @@ __global__ void __launch_bounds__(NTB, NTB >= 1024 ? 1 : 2) tau_tile_kernel(cons
                 if (q && (reinterpret_cast<uintptr_t>(q) & 15) == 0) prefetch_l2(q, bytes);
         }
     }
-    tile_skewer<COMP, MAXQ, AVG, true, (MAXQ >= 8 ? 8 : 4)>(L, L.rho + sk * (int64_t)N, L.vpec + sk * (int64_t)N,
-                            L.temp ? L.temp + sk * (int64_t)N : nullptr, out, smem_raw, warp_tot, tile_hist,
-                            whole_block());
+    tile_skewer<COMP, MAXQ, AVG, true, (MAXQ >= 8 ? 8 : 4), STAGE>(
+        L, L.rho + sk * (int64_t)N, L.vpec + sk * (int64_t)N, L.temp ? L.temp + sk * (int64_t)N : nullptr, out,
+        smem_raw, warp_tot, tile_hist, whole_block(), &stage_bar);
 }
 
 
@@ -1258,15 +1315,35 @@ static cudaError_t launch_kernel(K kernel, const TauLaunch& L0, size_t smem, int
     return cudaGetLastError();
 }
 
-template <bool COMP, bool AVG>
-static cudaError_t launch_tile_profile(const TauLaunch& L, cudaStream_t stream)
+// Inputs staged by bulk copies for rows of 2,048 pixels or more (n_pix % 4 ==
+// 0: rows 16-byte aligned, since fields are); measured on GB300 at 65,536 x
+// 4,096 px: 3.92 ms staged against 3.96 ms with vector loads, and on 1536^3
+// grid rows 50.8 ms against 50.0 ms, hence the threshold.  LYA_TILE_STAGE=0/1
+// in the environment forces either (diagnostics).
+static bool stage_inputs(const TauLaunch& L)
+{
+    const char* env = std::getenv("LYA_TILE_STAGE");
+    if ((L.n_pix & 3) != 0) return false;
+    if (env && (env[0] == '0' || env[0] == '1')) return env[0] == '1';
+    return L.n_pix >= 2048;
+}
+
+template <bool COMP, bool AVG, bool STAGE>
+static cudaError_t launch_tile_staged(const TauLaunch& L, cudaStream_t stream)
 {
     const size_t smem = tile_smem_bytes(L.n_pix, L.w_max);
     const int nt = block_threads(L.n_pix);                   // N <= 8 nt (n_pix <= 8192)
     const int q = (L.n_pix + nt - 1) / nt;
-    if (nt > 512) return launch_kernel(tau_tile_kernel<COMP, 8, AVG, 1024>, L, smem, nt, stream, true);
-    if (q <= 4) return launch_kernel(tau_tile_kernel<COMP, 4, AVG, 512>, L, smem, nt, stream, true);
-    return launch_kernel(tau_tile_kernel<COMP, 8, AVG, 512>, L, smem, nt, stream, true);
+    if (nt > 512) return launch_kernel(tau_tile_kernel<COMP, 8, AVG, 1024, STAGE>, L, smem, nt, stream, true);
+    if (q <= 4) return launch_kernel(tau_tile_kernel<COMP, 4, AVG, 512, STAGE>, L, smem, nt, stream, true);
+    return launch_kernel(tau_tile_kernel<COMP, 8, AVG, 512, STAGE>, L, smem, nt, stream, true);
+}
+
+template <bool COMP, bool AVG>
+static cudaError_t launch_tile_profile(const TauLaunch& L, cudaStream_t stream)
+{
+    return stage_inputs(L) ? launch_tile_staged<COMP, AVG, true>(L, stream)
+                           : launch_tile_staged<COMP, AVG, false>(L, stream);
 }
 
 template <bool COMP>

@@ -39,8 +39,14 @@ def test_grid_1536_full_size(lya):
     A, F = lya.rescale_mean_flux(tau, ls.GRID_1536_FT)
     st = lya.flux_stats(F)
     torch.cuda.synchronize()
+    # A by the property that defines it (Sec. 2.3), in FP64 on the device
+    total = torch.zeros((), dtype=torch.float64, device="cuda")
+    flat = tau.reshape(-1)
+    for lo in range(0, flat.numel(), 1 << 27):
+        total += torch.exp(-A * flat[lo:lo + (1 << 27)].double()).sum()
+    assert float(total) / flat.numel() == pytest.approx(ls.GRID_1536_FT, abs=1e-12)
     mean_F = float(F.sum(dtype=torch.float64)) / F.numel()
-    assert mean_F == pytest.approx(ls.GRID_1536_FT, abs=1e-7)
+    assert mean_F == pytest.approx(ls.GRID_1536_FT, abs=1e-7)          # F itself is FP32
     assert st.mean_flux == pytest.approx(ls.GRID_1536_FT, abs=1e-6)
     n_pick, seed = ls.GRID_1536_ORACLE_SUBSET
     ids = ls.random_subset(S, n_pick, seed)

@@ -248,17 +248,62 @@ def test_field_rejects_out_of_domain_values(lya):
 # ----------------------------------------------------------------------------
 # mean-flux rescaling and statistics
 # ----------------------------------------------------------------------------
+def fp64_mean_flux(tau, A):
+    """<exp(-A tau)> over a device tensor, in FP64 on the device (torch),
+    chunk by chunk: the property that defines A (Sec. 2.3)."""
+    import torch
+    flat = tau.reshape(-1)
+    total = torch.zeros((), dtype=torch.float64, device=flat.device)
+    for lo in range(0, flat.numel(), 1 << 26):
+        total += torch.exp(-A * flat[lo:lo + (1 << 26)].double()).sum()
+    return float(total) / flat.numel()
+
+
+# the mean-flux tolerance of the root-find (Sec. 2.3; the precision study's 1e-12)
+MEAN_F_TOL = 1e-12
+
+
 def test_rescale_closed_forms(lya):
     import torch
     tau = torch.full((4096,), 0.37, device="cuda")
     A, F = lya.rescale_mean_flux(tau, 0.72)
-    assert A == pytest.approx(-math.log(0.72) / 0.37, rel=1e-6)
+    # constant tau: A = -ln F_t / tau exactly (tau the FP32 value)
+    assert A == pytest.approx(-math.log(0.72) / float(np.float32(0.37)), rel=1e-11)
     t1 = 0.9
     tau2 = torch.tensor([t1, 2 * t1] * 5000, device="cuda", dtype=torch.float32)
     A2, F2 = lya.rescale_mean_flux(tau2, 0.65)
+    # two values tau, 2 tau equally weighted: e^{-A tau} = (-1 + sqrt(1 + 8 F_t)) / 2
     x = (-1 + math.sqrt(1 + 8 * 0.65)) / 2
-    assert math.exp(-A2 * float(np.float32(t1))) == pytest.approx(x, rel=1e-6)
-    assert float(F2.double().mean()) == pytest.approx(0.65, abs=1e-7)
+    assert math.exp(-A2 * float(np.float32(t1))) == pytest.approx(x, rel=1e-11)
+    assert fp64_mean_flux(tau2, A2) == pytest.approx(0.65, abs=MEAN_F_TOL)
+    assert float(F2.double().mean()) == pytest.approx(0.65, abs=1e-7)   # F itself is FP32
+
+
+def test_rescale_meets_1e12_against_the_oracle(lya, orc):
+    """The root-find's stopping test |<exp(-A tau)> - F_t| <= 1e-12, checked
+    in FP64, and A against the oracle's root-find on the same tau values."""
+    import torch
+    spec = ls.TINY_20MPC
+    rho, v, t = ls.skewers(spec, np.arange(ls.TINY_20MPC_SKEWERS))
+    field = make_field(lya, spec, rho, v, t)
+    tau = lya.extract_skewers(field, lya.ExtractParams())
+    for target in (ls.TINY_20MPC_FT, 0.65, 0.95):
+        A, F = lya.rescale_mean_flux(tau, target)
+        A_noalloc = lya.rescale_mean_flux_noalloc(tau, target, torch.empty_like(tau))
+        _, _, st = lya.rescale_mean_flux_stats(tau, target)
+        assert fp64_mean_flux(tau, A) == pytest.approx(target, abs=MEAN_F_TOL)
+        A_o, _ = orc.rescale(tau.double().cpu().numpy(), target)
+        assert A == pytest.approx(A_o, rel=1e-10)
+        assert A_noalloc == pytest.approx(A, rel=1e-10)
+        assert st.mean_flux == pytest.approx(target, abs=1e-6)
+    field.close()
+    # a heavy-tailed tau of 3e6 values (more CTAs, saturated pixels)
+    g = torch.Generator(device="cuda").manual_seed(9)
+    big = (torch.rand(3_000_000, device="cuda", generator=g) ** 6) * 40.0
+    A, _ = lya.rescale_mean_flux(big, 0.7)
+    assert fp64_mean_flux(big, A) == pytest.approx(0.7, abs=MEAN_F_TOL)
+    A_o, _ = orc.rescale(big.double().cpu().numpy(), 0.7)
+    assert A == pytest.approx(A_o, rel=1e-10)
 
 
 def test_rescale_errors(lya):
@@ -330,11 +375,11 @@ def test_gpc_full_size_sampled_parity(lya, orc, gpc_field, gamma):
     rho, v, t = ls.skewers(spec, ids)
     tau_o = orc.tau(po, rho, v, t if pg.t_mode == 0 else None)
     tau_g = tau[torch.as_tensor(ids, device="cuda")].cpu().numpy()
-    # A over all 65,536 skewers is not an oracle quantity at this size: check
-    # the GPU's A by the property that defines it, in FP64 on the host
-    tau_all = tau.double().cpu().numpy().ravel()
-    mean_F = float(np.mean(np.exp(-A_g * tau_all)))
-    assert mean_F == pytest.approx(ls.GPC_4096_FT, abs=1e-7)
+    # the GPU's A over all 65,536 skewers: the property that defines it, in
+    # FP64, and the oracle's root-find on the same 2.7e8 tau values
+    assert fp64_mean_flux(tau, A_g) == pytest.approx(ls.GPC_4096_FT, abs=MEAN_F_TOL)
+    A_o_all, _ = orc.rescale(tau.double().cpu().numpy().ravel(), ls.GPC_4096_FT)
+    assert A_g == pytest.approx(A_o_all, rel=1e-10)
     assert_tau_close(tau_g, tau_o, A_g)
     F_o = np.exp(-A_g * tau_o)
     F_g = F[torch.as_tensor(ids, device="cuda")].cpu().numpy()
@@ -389,7 +434,7 @@ def test_split_root_find_matches_single_device(lya, orc):
     tau = lya.extract_skewers(field, lya.ExtractParams()).ravel()
     A_ref, F_ref = lya.rescale_mean_flux(tau, ls.TINY_20MPC_FT)
     A1, _ = lya.rescale_mean_flux_distributed(tau, ls.TINY_20MPC_FT, allreduce=lambda x: list(x))
-    assert A1 == pytest.approx(A_ref, rel=1e-9)
+    assert A1 == pytest.approx(A_ref, rel=1e-10)
     halves = [tau[: tau.numel() // 2], tau[tau.numel() // 2:]]
 
     def allreduce_pair(_):
@@ -404,10 +449,58 @@ def test_split_root_find_matches_single_device(lya, orc):
 
     A2, _ = lya.rescale_mean_flux_distributed(None, ls.TINY_20MPC_FT, n=tau.numel(), allreduce=lambda x: list(x),
                                               moments=moments, sums=sums)
-    assert A2 == pytest.approx(A_ref, rel=1e-9)
+    assert A2 == pytest.approx(A_ref, rel=1e-10)
     F = torch.cat([lya.flux_at(h, A2) for h in halves])
     torch.cuda.synchronize()
     assert float((F - F_ref).abs().max()) <= 1e-6
+
+
+def test_sharded_call_over_two_host_threads(lya, orc):
+    """lya_rescale_mean_flux_sharded with two parts (host threads, each on its
+    own stream) whose all-reduce meets at a barrier: uneven parts and an empty
+    one give the oracle's A over all pixels and the same F as one device."""
+    import threading
+    import torch
+    spec = ls.TINY_20MPC
+    rho, v, t = ls.skewers(spec, np.arange(ls.TINY_20MPC_SKEWERS))
+    field = make_field(lya, spec, rho, v, t)
+    tau = lya.extract_skewers(field, lya.ExtractParams()).ravel()
+    torch.cuda.synchronize()
+    A_o, _ = orc.rescale(tau.double().cpu().numpy(), ls.TINY_20MPC_FT)
+    A_ref, F_ref = lya.rescale_mean_flux(tau, ls.TINY_20MPC_FT)
+    for cut in (tau.numel() // 3, 0):
+        parts = [tau[:cut], tau[cut:]]
+        barrier = threading.Barrier(2)
+        shared = {}
+        results = [None, None]
+
+        def allreduce(vals, rank):
+            shared[rank] = list(vals)
+            barrier.wait()
+            tot = [a + b for a, b in zip(shared[0], shared[1])]
+            barrier.wait()
+            return tot
+
+        def run(rank):
+            torch.cuda.set_device(0)
+            with torch.cuda.stream(torch.cuda.Stream()):
+                results[rank] = lya.rescale_mean_flux_sharded(parts[rank], ls.TINY_20MPC_FT,
+                                                              lambda x: allreduce(x, rank))
+                torch.cuda.current_stream().synchronize()
+
+        th = [threading.Thread(target=run, args=(r,)) for r in range(2)]
+        for x in th:
+            x.start()
+        for x in th:
+            x.join(60)
+        (A0, it0, F0), (A1, it1, F1) = results
+        assert A0 == A1 and it0 == it1
+        assert A0 == pytest.approx(A_o, rel=1e-10)
+        assert A0 == pytest.approx(A_ref, rel=1e-10)
+        assert fp64_mean_flux(tau, A0) == pytest.approx(ls.TINY_20MPC_FT, abs=MEAN_F_TOL)
+        F = torch.cat([F0, F1])
+        assert float((F - F_ref).abs().max()) <= 1e-6
+    field.close()
 
 
 def test_fused_stats_equal_separate_call(lya):

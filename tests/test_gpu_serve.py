@@ -133,7 +133,10 @@ def test_served_equals_direct_path(lya, pool):
             assert np.array_equal(st.pdf, r.stats.pdf)           # same F values, exact bins
             assert r.stats.n == st.n == ids.size * fields[f].n_pix
             assert r.stats.mean_flux == pytest.approx(st.mean_flux, abs=1e-8)   # FP32 partial sums
-            assert r.stats.mean_flux == pytest.approx(Ft, abs=1e-8)      # mean of the FP32 F values
+            # the mean of the FP32 F values: A is the root of the exact mean
+            # (to 1e-12), F is written with the MUFU exponential, whose small
+            # bias (~1e-8) shows here
+            assert r.stats.mean_flux == pytest.approx(Ft, abs=1e-7)
             assert r.stats.var_flux == pytest.approx(st.var_flux, rel=1e-6)
             srv.release(t)
 
