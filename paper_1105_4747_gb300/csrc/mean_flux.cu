@@ -17,9 +17,10 @@
 // e = 2^-y_hi (1 - y_lo ln 2), summed in compensated FP32 (g to ~1e-7: a fast
 // start that never ends the iteration; F itself is FP32).  The second Halley
 // pass forms e in double-float arithmetic to ~1e-15 (exp2_neg_precise) and
-// sums it in float pairs flushed to FP64, so g is known to ~1e-13; it ends the
-// iteration when |g| <= tol (1e-12) or when its Newton step is certified to
-// land within tol (halley_update).  CTAs and the final sums are FP64.
+// sums it in renormalised float pairs flushed to FP64 every 32 values, so g is
+// known to ~1e-13; it ends the iteration when |g| <= tol (1e-12) or when its
+// Newton step is certified to land within tol (halley_update).  CTAs and the
+// final sums are FP64.
 #include <cmath>
 #include <cstdint>
 #include <cstddef>
@@ -36,91 +37,56 @@ namespace {
 
 using namespace mfd;
 
-// ---- init pass: <tau>, zero and invalid counts, log-histogram, start value -------
-__global__ void __launch_bounds__(kThreads) mf_init_kernel(const float* __restrict__ tau, long long n,
-                                                         MFState* st, Partial* part)
+// ---- start value from a sample of tau ---------------------------------------------
+// Every (smask + 1)-th value (all of them for n <= 2^22, else at least 2^22,
+// a few MB read): the quarter-octave log-histogram and the mean of the
+// sample.  The last CTA starts A at -ln(F_t)/<tau>_sample, refined by the
+// root of the histogram proxy (proxy_start).  The checks over every value
+// (invalid values, all zero, too many zeros for a root) and the largest tau
+// come with the first Halley pass, which reads every value anyway.
+__global__ void __launch_bounds__(kThreads) mf_sample_kernel(const float* __restrict__ tau, long long n,
+                                                           MFState* st, Partial* part)
 {
-    // bins 0..kHistBins-1: log2 tau of a sample (every value for n <= 2^22,
-    // else every 2^k-th with at least 2^22 sampled); the extra slot counts the
-    // sample's zeros.  A start value needs no more than a sample.
-    __shared__ unsigned int h_s[kHistBins + 1];
+    __shared__ unsigned int h_s[kHistBins + 1];            // + the sample's zeros
     for (int b = threadIdx.x; b <= kHistBins; b += blockDim.x) h_s[b] = 0;
     __syncthreads();
     long long smask = 0;
     while ((n >> 22) > smask) smask = 2 * smask + 1;        // sample stride - 1 (a power of 2 minus 1)
+    const long long ns = (n + smask) / (smask + 1);
     KahanF32 s;
-    unsigned int z = 0, bad = 0;                            // per thread: far below 2^32 values
-    float tmax = 0.f;
-    auto take = [&](float t) {
-        if (!(t >= 0.f) || !isfinite(t)) {
-            ++bad;
-            return;
-        }
-        s.add(t);
-        z += (t == 0.f);
-        tmax = fmaxf(tmax, t);
-    };
-    auto sample = [&](float t) {
-        if (t >= 0.f && isfinite(t)) atomicAdd(&h_s[t == 0.f ? kHistBins : hist_bin(t)], 1u);
-    };
+    unsigned int z = 0, cnt = 0;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x, nthr = (long long)gridDim.x * blockDim.x;
-    if (smask >= 3 && (reinterpret_cast<uintptr_t>(tau) & 15) == 0) {
-        // a stride of at least four: only the first value of a float4 whose
-        // index is a multiple of the stride is sampled (same values, same
-        // order as the general loop below)
-        const float4* __restrict__ t4 = reinterpret_cast<const float4*>(tau);
-        const long long n4 = n >> 2;
-        long long i = tid;
-        for (; i + 7 * nthr < n4; i += 8 * nthr) {
-            float4 v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = t4[i + u * nthr];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                take(v[u].x);
-                take(v[u].y);
-                take(v[u].z);
-                take(v[u].w);
-                if (((4 * (i + u * nthr)) & smask) == 0) sample(v[u].x);
-            }
-        }
-        for (; i < n4; i += nthr) {
-            const float4 v = t4[i];
-            take(v.x);
-            take(v.y);
-            take(v.z);
-            take(v.w);
-            if (((4 * i) & smask) == 0) sample(v.x);
-        }
-        for (long long k = 4 * n4 + tid; k < n; k += nthr) {
-            take(tau[k]);
-            if ((k & smask) == 0) sample(tau[k]);
-        }
-    } else {
-        stream_f32(tau, n, [&](long long i, float t) {
-            take(t);
-            if ((i & smask) == 0) sample(t);
-        });
+    for (long long k = tid; k < ns; k += nthr) {
+        const float t = tau[k * (smask + 1)];
+        if (!(t >= 0.f) || !isfinite(t)) continue;
+        s.add(t);
+        ++cnt;
+        z += (t == 0.f);
+        atomicAdd(&h_s[t == 0.f ? kHistBins : hist_bin(t)], 1u);
     }
     __shared__ double sh[3][32];
-    double v[3] = {(double)s.value(), (double)z, (double)bad};
+    double v[3] = {(double)s.value(), (double)z, (double)cnt};
     block_sum<3>(v, sh);
-    for (int o = 16; o > 0; o >>= 1) tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(&st->tau_max_bits, __float_as_uint(tmax));
     for (int b = threadIdx.x; b <= kHistBins; b += blockDim.x)
         if (h_s[b]) atomicAdd(&st->hist[b], (unsigned long long)h_s[b]);
     if (threadIdx.x == 0) part[blockIdx.x] = Partial{v[0], 0.0, 0.0, 0.0, (long long)v[1], (long long)v[2]};
     if (!last_block(&st->ticket)) return;
-
-    // the last block: totals, domain checks, then the histogram proxy's root
-    __shared__ int s_go;
     double tot[3];
     partial_totals<3>(part, gridDim.x, tot, sh, [](const Partial& p, double (&x)[3]) {
         x[0] = p.s0; x[1] = (double)p.z; x[2] = (double)p.bad;
     });
-    if (threadIdx.x == 0) s_go = init_finish(st, tot[0], (long long)tot[1], (long long)tot[2]);
+    if (threadIdx.x == 0) {
+        st->ticket = 0;
+        const double mean = tot[2] > 0.0 ? tot[0] / tot[2] : 0.0;
+        st->A = mean > 0.0 ? -log(st->Ft) / mean : 1.0;
+        st->lo = 0.0;
+        st->hi = INFINITY;
+        st->iter = 0;
+        st->done = 0;
+        st->status = LYA_ENOCONV;                    // until converged
+    }
     __syncthreads();
-    if (s_go) proxy_start(st);
+    proxy_start(st);
 }
 
 // ---- the root-find state set on the device (no host copy to wait for) -----------
@@ -152,27 +118,30 @@ __global__ void __launch_bounds__(kThreads) mf_newton_kernel(const float* __rest
     if constexpr (PRECISE) load_exp2_table(tab);
     float a_hi, a_lo;
     split_rate(st->A, a_hi, a_lo);
-    __shared__ double sh[4][32];
-    double v[4];
+    __shared__ double sh[6][32];
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
     if constexpr (PRECISE) {
-        DFSum s0;
+        DFSum s0;                                     // sum e to ~1e-13 (float pairs, FP64)
         KahanF32 s1;                                  // g' enters the step's certificate
         float s2 = 0.f;
-        stream_f32(tau, n, [&](long long, float t) {
+        stream_f32_steps(tau, n, (long long)blockIdx.x * blockDim.x + threadIdx.x,
+                         (long long)gridDim.x * blockDim.x, [&](float t) {
             float eh, el;
             exp2_neg_precise(t, a_hi, a_lo, tab, eh, el);
             s0.add(eh, el);
             const float te = t * eh;
             s1.add(te);
             s2 = fmaf(t, te, s2);
-        });
+        }, [&] { s0.flush(); });
         v[0] = s0.value();
         v[1] = 0.0;
         v[2] = (double)s1.s - (double)s1.c;
         v[3] = (double)s2;
-    } else {
+    }
+    unsigned int z = 0, bad = 0;                      // (the fast pass: checks over every value)
+    if constexpr (!PRECISE) {
         KahanF32 s0;
-        float s0c = 0.f, s1 = 0.f, s2 = 0.f;
+        float s0c = 0.f, s1 = 0.f, s2 = 0.f, tmax = 0.f;
         stream_f32(tau, n, [&](long long, float t) {
             float e, c;
             exp_neg(t, a_hi, a_lo, e, c);
@@ -181,20 +150,38 @@ __global__ void __launch_bounds__(kThreads) mf_newton_kernel(const float* __rest
             const float te = t * e;
             s1 += te;
             s2 = fmaf(t, te, s2);
+            bad += !(t >= 0.f && t <= 3.4e38f);       // negative, NaN or infinite
+            z += (t == 0.f);
+            tmax = fmaxf(tmax, t);
         });
         v[0] = (double)s0.value();
         v[1] = (double)s0c;
         v[2] = (double)s1;
         v[3] = (double)s2;
+        for (int o = 16; o > 0; o >>= 1) tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+        if ((threadIdx.x & 31) == 0 && tmax > 0.f) atomicMax(&st->tau_max_bits, __float_as_uint(tmax));
     }
     block_sum<4>(v, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = Partial{v[0], v[1], v[2], v[3], 0, 0};
+    double zb[2] = {(double)z, (double)bad};
+    if constexpr (!PRECISE) block_sum<2>(zb, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = Partial{v[0], v[1], v[2], v[3], (long long)zb[0], (long long)zb[1]};
     if (!last_block(&st->ticket)) return;
-    double tot[4];
-    partial_totals<4>(part, gridDim.x, tot, sh, [](const Partial& p, double (&x)[4]) {
-        x[0] = p.s0; x[1] = p.s0c; x[2] = p.s1; x[3] = p.s2;
+    double tot[6];
+    partial_totals<6>(part, gridDim.x, tot, sh, [](const Partial& p, double (&x)[6]) {
+        x[0] = p.s0; x[1] = p.s0c; x[2] = p.s1; x[3] = p.s2; x[4] = (double)p.z; x[5] = (double)p.bad;
     });
-    if (threadIdx.x == 0) halley_update(st, tot[0], tot[1], tot[2], tot[3], PRECISE);
+    if (threadIdx.x == 0) {
+        const double nn = (double)n;
+        if (!PRECISE && (tot[5] > 0.0 || tot[4] >= nn)) {         // invalid values, or all zero
+            st->status = LYA_EINVAL;
+            st->done = 1;
+        } else if (!PRECISE && tot[4] / nn >= st->Ft) {          // <e^{-A tau}> >= zero fraction: no root
+            st->status = LYA_ENOCONV;
+            st->done = 1;
+        } else {
+            halley_update(st, tot[0], tot[1], tot[2], tot[3], PRECISE);
+        }
+    }
 }
 
 // ---- F = exp(-A tau), the convergence check at that A and, optionally, the
@@ -488,10 +475,11 @@ cudaError_t launch_field_check(const float* rho, const float* vpec, const float*
 
 namespace {
 
-// The host side of one root-find on caller-chosen scratch: the init pass,
-// then rounds of two Halley passes (MUFU, then precise: the latter decides
-// convergence) and one flux pass (which writes F, if asked, at the final A),
-// reading the state back once per round.
+// The host side of one root-find on caller-chosen scratch: the sample pass
+// (start value), then rounds of two Halley passes (MUFU with the checks over
+// every value, then precise: the latter decides convergence) and one flux pass
+// (which writes F, if asked, at the final A), reading the state back once per
+// round.
 static lya_status solve_on_scratch(const float* tau, int64_t n, double target, double tol, int max_iter,
                                    double* A_out, float* flux_out, MFState* st, Partial* part, int grid,
                                    cudaStream_t stream, StatPart* spart = nullptr, StatsOut* sout = nullptr,
@@ -508,7 +496,7 @@ static lya_status solve_on_scratch(const float* tau, int64_t n, double target, d
     count_launch();
     cudaError_t err = cudaGetLastError();
     if (err == cudaSuccess) {
-        mf_init_kernel<<<grid, kThreads, 0, stream>>>(tau, n, st, part);
+        mf_sample_kernel<<<grid, kThreads, 0, stream>>>(tau, n, st, part);
         count_launch();
         err = cudaGetLastError();
     }
@@ -739,14 +727,15 @@ __global__ void __launch_bounds__(kThreads) mf_sums_kernel(const float* __restri
     DFSum s0;                                   // sum e precise (double-float exponentials)
     KahanF32 s1;
     float s2 = 0.f;
-    stream_f32(tau, n, [&](long long, float t) {
+    stream_f32_steps(tau, n, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x,
+                     [&](float t) {
         float eh, el;
         exp2_neg_precise(t, a_hi, a_lo, tab, eh, el);
         s0.add(eh, el);
         const float te = t * eh;
         s1.add(te);
         s2 = fmaf(t, te, s2);
-    });
+    }, [&] { s0.flush(); });
     __shared__ double sh[4][32];
     double v[4] = {s0.value(), 0.0, (double)s1.s - (double)s1.c, (double)s2};
     block_sum<4>(v, sh);

@@ -57,6 +57,45 @@ __device__ __forceinline__ void stream_f32(const float* __restrict__ x, long lon
     stream_f32(x, n, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x, f);
 }
 
+// stream_f32 with done() called after every step of at most 32 values per
+// thread (the fixed-point sums move their integer part into FP64 there).
+template <typename Fn, typename Done>
+__device__ __forceinline__ void stream_f32_steps(const float* __restrict__ x, long long n, long long tid,
+                                                 long long nthr, Fn&& f, Done&& done)
+{
+    if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {
+        const float4* __restrict__ x4 = reinterpret_cast<const float4*>(x);
+        const long long n4 = n >> 2;
+        long long i = tid;
+        for (; i + 7 * nthr < n4; i += 8 * nthr) {
+            float4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = x4[i + u * nthr];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                f(v[u].x); f(v[u].y); f(v[u].z); f(v[u].w);
+            }
+            done();
+        }
+        for (; i < n4; i += nthr) {
+            const float4 v = x4[i];
+            f(v.x); f(v.y); f(v.z); f(v.w);
+            done();
+        }
+        for (long long k = 4 * n4 + tid; k < n; k += nthr) f(x[k]);
+    } else {
+        int c = 0;
+        for (long long k = tid; k < n; k += nthr) {
+            f(x[k]);
+            if (++c == 32) {
+                done();
+                c = 0;
+            }
+        }
+    }
+    done();
+}
+
 // Quarter-octave histogram of log2(tau) over [2^-64, 2^64), built in the
 // init pass; its bin centres give a cheap proxy of g(A) whose root starts
 // the exact iteration close to the answer.
@@ -200,8 +239,7 @@ __device__ __forceinline__ void exp_neg(float t, float a_hi, float a_lo, float& 
 //   2^-y = 2^-(N >> 10) * 2^(-(N & 1023)/1024) * exp(u),  u = -(r + y_lo) ln 2,
 // the middle factor a double-float from kExp2Tab (in shared memory), exp(u) =
 // 1 + u + u^2/2 + u^3/6 with |u| <= 3.4e-4 (the next term is below 6e-16),
-// u itself a double-float (ln 2 split into two floats).  Values with
-// y >= 125 (e < 3e-38) are returned as 0.  Result: e_hi + e_lo.
+// u itself a double-float (ln 2 split into two floats).  Result: e_hi + e_lo.
 constexpr float kLn2Hi = 0x1.62e430p-1f;                 // float nearest ln 2
 constexpr float kLn2Lo = -0x1.05c610p-29f;               // ln 2 - kLn2Hi, to float
 
@@ -212,16 +250,13 @@ __device__ __forceinline__ void load_exp2_table(float2* tab)
     __syncthreads();
 }
 
+// (y is clamped at 100, where e < 1e-30 and its value no longer matters.)
 __device__ __forceinline__ void exp2_neg_precise(float t, float a_hi, float a_lo, const float2* __restrict__ tab,
                                                  float& e_hi, float& e_lo)
 {
-    const float y_hi = t * a_hi;
-    const float y_lo = fmaf(t, a_lo, fmaf(t, a_hi, -y_hi));
-    if (!(y_hi < 125.f)) {
-        e_hi = 0.f;
-        e_lo = 0.f;
-        return;
-    }
+    const float y_raw = t * a_hi;
+    const float y_hi = fminf(y_raw, 100.f);
+    const float y_lo = y_raw <= 100.f ? fmaf(t, a_lo, fmaf(t, a_hi, -y_hi)) : 0.f;
     const float Nf = rintf(y_hi * 1024.f);
     const int N = (int)Nf;
     const float r = fmaf(Nf, -1.f / 1024.f, y_hi);                     // exact
@@ -241,26 +276,28 @@ __device__ __forceinline__ void exp2_neg_precise(float t, float a_hi, float a_lo
     e_lo = R_lo * scale;
 }
 
-// Per-thread sum of e_hi + e_lo values: a float pair updated with an exact
-// two-sum, moved into an FP64 total every 32 terms so the pair's rounding
-// never builds up.
+// Per-thread sum of e_hi + e_lo values: a float pair (h, l) with |l| <=
+// ulp(h)/2 after every addition (an exact two-sum, then the pair
+// renormalised), so each addition errs by at most ~2^-48 of the pair's value;
+// flush() moves the pair into an FP64 total after every stream step of at
+// most 32 values, which bounds the pair's relative error by 32 * 2^-48 ~ 1e-13.
 struct DFSum {
     double acc = 0.0;
     float h = 0.f, l = 0.f;
-    int k = 0;
     __device__ __forceinline__ void add(float eh, float el)
     {
         const float s = __fadd_rn(h, eh);
         const float bp = __fsub_rn(s, h);
         const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(eh, bp));
-        l = __fadd_rn(l, __fadd_rn(err, el));
-        h = s;
-        if (++k == 32) {
-            acc += (double)h + (double)l;
-            h = 0.f;
-            l = 0.f;
-            k = 0;
-        }
+        const float t = __fadd_rn(l, __fadd_rn(err, el));
+        h = __fadd_rn(s, t);                          // renormalise: h + l = s + t exactly
+        l = __fsub_rn(t, __fsub_rn(h, s));
+    }
+    __device__ __forceinline__ void flush()
+    {
+        acc += (double)h + (double)l;
+        h = 0.f;
+        l = 0.f;
     }
     __device__ __forceinline__ double value() const { return acc + ((double)h + (double)l); }
 };
@@ -340,10 +377,10 @@ __device__ inline void proxy_start(MFState* st)
 // the iteration; only a precise pass (g to ~1e-13) decides convergence.
 constexpr double kApproxGErr = 1e-6;
 // Bounds used by the precise pass's certificate: on the error of its g
-// (double-float exponentials, ~1e-15 per term, float-pair partial sums of 32
-// terms, FP64 beyond) and on the relative error of its g' (compensated FP32
-// per thread, FP64 beyond).
-constexpr double kPreciseGErr = 1e-13;
+// (double-float exponentials, ~1e-14 per term at worst; float-pair partial
+// sums of at most 32 terms, ~1e-13 relative at worst; FP64 beyond) and on
+// the relative error of its g' (compensated FP32 per thread, FP64 beyond).
+constexpr double kPreciseGErr = 2e-13;
 constexpr double kSlopeRelErr = 1e-5;
 
 __host__ __device__ inline bool finite_d(double x) { return x == x && x - x == 0.0; }

@@ -157,14 +157,14 @@ __global__ void __launch_bounds__(kRfThreads) rf_halley_kernel(const unsigned ch
             DFSum s0;
             KahanF32 s1;                              // g' enters the step's certificate
             float s2 = 0.f;
-            stream_f32(s.tau + U.begin, U.end - U.begin, threadIdx.x, blockDim.x, [&](long long, float t) {
+            stream_f32_steps(s.tau + U.begin, U.end - U.begin, threadIdx.x, blockDim.x, [&](float t) {
                 float eh, el;
                 exp2_neg_precise(t, a_hi, a_lo, tab, eh, el);
                 s0.add(eh, el);
                 const float te = t * eh;
                 s1.add(te);
                 s2 = fmaf(t, te, s2);
-            });
+            }, [&] { s0.flush(); });
             x[0] = s0.value();
             x[1] = 0.0;
             x[2] = (double)s1.s - (double)s1.c;

@@ -462,6 +462,14 @@ __device__ __forceinline__ float cell_erf(float y, float hw)
     return erfcf(ay - hw) - erfcf(ay + hw);
 }
 
+// The same for the cell between edges a < b from Ea = erfc(|a|), Eb =
+// erfc(|b|), so that adjacent cells share their common edge's erfc: a cell
+// right of 0 is Ea - Eb, left of 0 Eb - Ea, across 0 2 - Ea - Eb.
+__device__ __forceinline__ float cell_from_edges(float a, float b, float Ea, float Eb)
+{
+    return a >= 0.f ? Ea - Eb : (b <= 0.f ? Eb - Ea : (2.f - Ea) - Eb);
+}
+
 // Two adjacent pixels fo, fo + 1 (in the run's frame) against candidates [k0, k1).
 // Records {a, c r, lw, t} (sampled profile: term 2^(lw - x^2)); AVG: records
 // hold the averaged-profile constants {du/b, r/b, w sqrt(pi) b/2du, t}.
@@ -473,9 +481,11 @@ __device__ __forceinline__ void pair2_segment(const float4* __restrict__ rec, in
         const float x0 = fmaf(fo - r.w, r.x, -r.y);                  // r = {a, c r, w, t}
         const float x1 = x0 + r.x;
         if constexpr (AVG) {
-            const float hw = 0.5f * r.x;
-            t0 = r.z * cell_erf(x0, hw);
-            t1 = r.z * cell_erf(x1, hw);
+            // the two cells' three edges, each erfc once
+            const float e0 = fmaf(-0.5f, r.x, x0), e1 = fmaf(0.5f, r.x, x0), e2 = fmaf(1.5f, r.x, x0);
+            const float E0 = erfcf(fabsf(e0)), E1 = erfcf(fabsf(e1)), E2 = erfcf(fabsf(e2));
+            t0 = r.z * cell_from_edges(e0, e1, E0, E1);
+            t1 = r.z * cell_from_edges(e1, e2, E1, E2);
         } else {
             t0 = ex2(fmaf(-x0, x0, r.z));                             // r.z = lw
             t1 = ex2(fmaf(-x1, x1, r.z));
@@ -615,8 +625,15 @@ __device__ __forceinline__ void pair4_segment(const float4* __restrict__ rec, in
     auto terms = [&](const float4& r, float (&t)[4]) {
         const float x0 = fmaf(fo - r.w, r.x, -r.y);                  // r = {a, c r, w, t}
         if constexpr (AVG) {
+            // the four cells' five edges, each erfc once
+            float e[5], E[5];
 #pragma unroll
-            for (int m = 0; m < 4; ++m) t[m] = r.z * cell_erf(fmaf((float)m, r.x, x0), 0.5f * r.x);
+            for (int m = 0; m < 5; ++m) {
+                e[m] = fmaf((float)m - 0.5f, r.x, x0);
+                E[m] = erfcf(fabsf(e[m]));
+            }
+#pragma unroll
+            for (int m = 0; m < 4; ++m) t[m] = r.z * cell_from_edges(e[m], e[m + 1], E[m], E[m + 1]);
         } else if constexpr (EXP == LYA_EXP_RECURRENCE) {
             if (r.x <= kRecMaxA) {
                 float E = ex2(-(x0 * x0));

@@ -36,15 +36,23 @@ def flux_lines(lya, n_los, n_pix, box, seed):
     return F
 
 
-@pytest.mark.parametrize("n_perp,n_pix,fill,noise", [(16, 512, 1.0, 0.0), (12, 768, 0.4, 0.05), (32, 256, 0.3, 0.0)])
-def test_flux_power_3d_matches_oracle(lya, n_perp, n_pix, fill, noise):
+@pytest.mark.parametrize("n_perp,n_pix,fill,noise,box", [(16, 512, 1.0, 0.0, 200.0), (12, 768, 0.4, 0.05, 200.0),
+                                                         (32, 256, 0.3, 0.0, 200.0),
+                                                         # the size bench.py times: 4,096 lines of 4,096 px
+                                                         # filling a 64 x 64 grid across a 1 h^-1 Gpc box
+                                                         (64, 4096, 1.0, 0.0, 1000.0), (64, 4096, 1.0, 0.05, 1000.0)])
+def test_flux_power_3d_matches_oracle(lya, n_perp, n_pix, fill, noise, box):
     from oracle import flux3d as f3
-    box = 200.0
     rng = np.random.default_rng(n_perp * 1000 + n_pix)
     all_cells = np.array([(i, j) for i in range(n_perp) for j in range(n_perp)])
     pick = all_cells[rng.permutation(len(all_cells))[: max(2, int(fill * len(all_cells)))]]
     F = flux_lines(lya, len(pick), n_pix, box, seed=40 + n_perp)
-    k, pt, pb, nm = lya.flux_power_3d(F, pick, n_perp, box, noise)
+    if fill == 1.0 and n_perp == 64:
+        # as bench.py calls it: line i at flat cell i (ix * n_perp + iy)
+        pick = np.stack([np.arange(len(pick)) // n_perp, np.arange(len(pick)) % n_perp], axis=1)
+        k, pt, pb, nm = lya.flux_power_3d(F, np.arange(len(pick)), n_perp, box, noise)
+    else:
+        k, pt, pb, nm = lya.flux_power_3d(F, pick, n_perp, box, noise)
     ko, pto, pbo, nmo = f3.flux_power_3d(F.cpu().numpy(), pick, n_perp, box, noise)
     assert len(k) == len(ko)
     assert np.array_equal(nm, nmo)
