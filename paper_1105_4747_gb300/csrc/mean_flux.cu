@@ -16,7 +16,7 @@
 // exponential of a double-float argument y = tau A log2(e) = y_hi + y_lo,
 // e = 2^-y_hi (1 - y_lo ln 2), summed in compensated FP32 (g to ~1e-7: a fast
 // start that never ends the iteration; F itself is FP32).  The second Halley
-// pass forms e in double-float arithmetic to ~1e-15 (exp2_neg_precise) and
+// pass forms e in double-float arithmetic to ~3e-14 (exp2_neg_precise) and
 // sums it in renormalised float pairs flushed to FP64 every 32 values, so g is
 // known to ~1e-13; it ends the iteration when |g| <= tol (1e-12) or when its
 // Newton step is certified to land within tol (halley_update).  CTAs and the

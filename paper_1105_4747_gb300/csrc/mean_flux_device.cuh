@@ -230,7 +230,7 @@ __device__ __forceinline__ void exp_neg(float t, float a_hi, float a_lo, float& 
     corr = -e * y_lo * kLn2f;
 }
 
-// ---- precise passes: e = 2^-y to ~1e-15 relative on the FP32 pipe -----------------
+// ---- precise passes: e = 2^-y to ~3e-14 on the FP32 pipe -------------------------
 // GB300 runs FP64 at a small fraction of its FP32 rate, so a per-pixel FP64
 // exponential would cost milliseconds per pass over 2.7e8 pixels; instead the
 // exponential is formed in double-float arithmetic (pairs of floats) from the
@@ -239,7 +239,11 @@ __device__ __forceinline__ void exp_neg(float t, float a_hi, float a_lo, float& 
 //   2^-y = 2^-(N >> 10) * 2^(-(N & 1023)/1024) * exp(u),  u = -(r + y_lo) ln 2,
 // the middle factor a double-float from kExp2Tab (in shared memory), exp(u) =
 // 1 + u + u^2/2 + u^3/6 with |u| <= 3.4e-4 (the next term is below 6e-16),
-// u itself a double-float (ln 2 split into two floats).  Result: e_hi + e_lo.
+// u itself a double-float (ln 2 split into two floats).  Result: e_hi + e_lo,
+// within ~3e-14 absolute for every y (what the mean of e needs): near e = 1
+// the float pair's last rounding (~2^-46) sets it; at large y the relative
+// error grows as ~1.5e-15 y^2 (the series omits the higher terms of u_lo ~
+// y_lo ln 2) on values that shrink as 2^-y.
 constexpr float kLn2Hi = 0x1.62e430p-1f;                 // float nearest ln 2
 constexpr float kLn2Lo = -0x1.05c610p-29f;               // ln 2 - kLn2Hi, to float
 
@@ -377,7 +381,7 @@ __device__ inline void proxy_start(MFState* st)
 // the iteration; only a precise pass (g to ~1e-13) decides convergence.
 constexpr double kApproxGErr = 1e-6;
 // Bounds used by the precise pass's certificate: on the error of its g
-// (double-float exponentials, ~1e-14 per term at worst; float-pair partial
+// (double-float exponentials, ~3e-14 per term at worst; float-pair partial
 // sums of at most 32 terms, ~1e-13 relative at worst; FP64 beyond) and on
 // the relative error of its g' (compensated FP32 per thread, FP64 beyond).
 constexpr double kPreciseGErr = 2e-13;
