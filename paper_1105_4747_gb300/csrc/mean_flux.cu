@@ -12,15 +12,17 @@
 // and updates A in device memory, so passes chain on the stream without a
 // host round trip.  A pass launched after convergence returns at once.
 //
-// Precision: the first Halley pass of a round and the flux pass use the MUFU
-// exponential of a double-float argument y = tau A log2(e) = y_hi + y_lo,
-// e = 2^-y_hi (1 - y_lo ln 2), summed in compensated FP32 (g to ~1e-7: a fast
-// start that never ends the iteration; F itself is FP32).  The second Halley
-// pass forms e in double-float arithmetic to ~3e-14 (exp2_neg_precise) and
-// sums it in renormalised float pairs flushed to FP64 every 32 values, so g is
-// known to ~1e-13; it ends the iteration when |g| <= tol (1e-12) or when its
-// Newton step is certified to land within tol (halley_update).  CTAs and the
-// final sums are FP64.
+// Precision: the first Halley pass of a round uses the MUFU exponential of a
+// double-float argument y = tau A log2(e) = y_hi + y_lo, e = 2^-y_hi (1 - y_lo
+// ln 2), summed in compensated FP32 (g to ~1e-7: a fast start that never ends
+// the iteration).  The second Halley pass forms e in double-float arithmetic
+// to ~3e-14 (exp2_neg_precise) and sums it in renormalised float pairs
+// flushed to FP64 every 32 values, so g is known to ~1e-13; it ends the
+// iteration when |g| <= tol (1e-12) or when its Newton step is certified to
+// land within tol (halley_update).  It also writes F = e rounded to FP32,
+// which is final when its step moved A too little to change F by more than
+// kFluxShift; otherwise a flux pass (MUFU exponential) writes F at the final
+// A.  CTAs and the final sums are FP64.
 #include <cmath>
 #include <cstdint>
 #include <cstddef>
@@ -105,65 +107,48 @@ __global__ void __launch_bounds__(kThreads) mf_state_init_kernel(MFState* st, do
     }
 }
 
-// ---- one Halley pass: g, g' and g'' in one read of tau -----------------------------
-// PRECISE: sum e in double-float (exp2_neg_precise), so g is known to ~1e-13
-// and the pass may end the iteration; else the MUFU exponential with its
-// first-order argument correction (g to ~1e-7), a fast start.
-template <bool PRECISE>
+// ---- the fast Halley pass: g, g' and g'' in one read of tau ------------------------
+// The FP32 polynomial exponential (exp2_neg_fast: no systematic bias beyond
+// ~1e-9), summed in FP32 over steps of at most 32 values and in
+// FP64 across them: g to ~1e-9 in practice, but with no bound that could end
+// the iteration, so it is a start for the precise pass, close enough that the
+// precise pass's step seldom moves F.  It also makes the checks over every
+// value (invalid values, all zero, too many zeros for a root) and finds the
+// largest tau: t + 0 maps -0 to +0, and the largest of those float bits as
+// unsigned is above 0x7f7fffff exactly when some value is negative, infinite
+// or NaN, else it is the bits of the largest tau.
 __global__ void __launch_bounds__(kThreads) mf_newton_kernel(const float* __restrict__ tau, long long n,
                                                            MFState* st, Partial* part)
 {
     if (st->done) return;
-    __shared__ float2 tab[PRECISE ? kExp2TabSize : 1];
-    if constexpr (PRECISE) load_exp2_table(tab);
     float a_hi, a_lo;
     split_rate(st->A, a_hi, a_lo);
     __shared__ double sh[6][32];
     double v[4] = {0.0, 0.0, 0.0, 0.0};
-    if constexpr (PRECISE) {
-        DFSum s0;                                     // sum e to ~1e-13 (float pairs, FP64)
-        KahanF32 s1;                                  // g' enters the step's certificate
-        float s2 = 0.f;
-        stream_f32_steps(tau, n, (long long)blockIdx.x * blockDim.x + threadIdx.x,
-                         (long long)gridDim.x * blockDim.x, [&](float t) {
-            float eh, el;
-            exp2_neg_precise(t, a_hi, a_lo, tab, eh, el);
-            s0.add(eh, el);
-            const float te = t * eh;
-            s1.add(te);
-            s2 = fmaf(t, te, s2);
-        }, [&] { s0.flush(); });
-        v[0] = s0.value();
-        v[1] = 0.0;
-        v[2] = (double)s1.s - (double)s1.c;
-        v[3] = (double)s2;
-    }
-    unsigned int z = 0, bad = 0;                      // (the fast pass: checks over every value)
-    if constexpr (!PRECISE) {
-        KahanF32 s0;
-        float s0c = 0.f, s1 = 0.f, s2 = 0.f, tmax = 0.f;
-        stream_f32(tau, n, [&](long long, float t) {
-            float e, c;
-            exp_neg(t, a_hi, a_lo, e, c);
-            s0.add(e);
-            s0c += c;
-            const float te = t * e;
-            s1 += te;
-            s2 = fmaf(t, te, s2);
-            bad += !(t >= 0.f && t <= 3.4e38f);       // negative, NaN or infinite
-            z += (t == 0.f);
-            tmax = fmaxf(tmax, t);
-        });
-        v[0] = (double)s0.value();
-        v[1] = (double)s0c;
-        v[2] = (double)s1;
-        v[3] = (double)s2;
-        for (int o = 16; o > 0; o >>= 1) tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
-        if ((threadIdx.x & 31) == 0 && tmax > 0.f) atomicMax(&st->tau_max_bits, __float_as_uint(tmax));
-    }
+    unsigned int z = 0, umax = 0;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    stream_f32_steps(tau, n, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x,
+                     [&](float t) {
+        const float e = exp2_neg_fast(t, a_hi, a_lo);
+        s0 += e;
+        const float te = t * e;
+        s1 += te;
+        s2 = fmaf(t, te, s2);
+        const unsigned int b = __float_as_uint(t + 0.f);
+        umax = max(umax, b);
+        z += (b == 0u);
+    }, [&] {
+        v[0] += (double)s0;
+        v[2] += (double)s1;
+        v[3] += (double)s2;
+        s0 = s1 = s2 = 0.f;
+    });
+    umax = __reduce_max_sync(0xffffffffu, umax);
+    const bool bad = umax > 0x7f7fffffu;
+    if ((threadIdx.x & 31) == 0 && umax > 0u && !bad) atomicMax(&st->tau_max_bits, umax);
     block_sum<4>(v, sh);
-    double zb[2] = {(double)z, (double)bad};
-    if constexpr (!PRECISE) block_sum<2>(zb, sh);
+    double zb[2] = {(double)z, bad ? 1.0 : 0.0};
+    block_sum<2>(zb, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = Partial{v[0], v[1], v[2], v[3], (long long)zb[0], (long long)zb[1]};
     if (!last_block(&st->ticket)) return;
     double tot[6];
@@ -172,32 +157,207 @@ __global__ void __launch_bounds__(kThreads) mf_newton_kernel(const float* __rest
     });
     if (threadIdx.x == 0) {
         const double nn = (double)n;
-        if (!PRECISE && (tot[5] > 0.0 || tot[4] >= nn)) {         // invalid values, or all zero
+        if (tot[5] > 0.0 || tot[4] >= nn) {                      // invalid values, or all zero
             st->status = LYA_EINVAL;
             st->done = 1;
-        } else if (!PRECISE && tot[4] / nn >= st->Ft) {          // <e^{-A tau}> >= zero fraction: no root
+        } else if (tot[4] / nn >= st->Ft) {                      // <e^{-A tau}> >= zero fraction: no root
             st->status = LYA_ENOCONV;
             st->done = 1;
         } else {
-            halley_update(st, tot[0], tot[1], tot[2], tot[3], PRECISE);
+            halley_update(st, tot[0], tot[1], tot[2], tot[3], false);
         }
     }
 }
 
-// ---- F = exp(-A tau), the convergence check at that A and, optionally, the
-//      statistics of that F (kept only when the check passes) ---------------
 struct StatsOut {
     double m1, m2;                // sums of (F - 0.5) and (F - 0.5)^2
     unsigned long long pdf[21];
     unsigned int ticket;
 };
 
+// Sums the per-CTA statistics into *sout (the last CTA, all of its threads).
+__device__ inline void stats_totals(const StatPart* spart, StatsOut* sout, double (*sh)[32])
+{
+    double ms[2] = {0.0, 0.0};
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+        ms[0] += spart[b].m1;
+        ms[1] += spart[b].m2;
+    }
+    block_sum<2>(ms, sh);
+    for (int k = threadIdx.x; k < 21; k += blockDim.x) {
+        unsigned long long c = 0;
+        for (int b = 0; b < (int)gridDim.x; ++b) c += spart[b].pdf[k];
+        sout->pdf[k] = c;
+    }
+    if (threadIdx.x == 0) {
+        sout->m1 = ms[0];
+        sout->m2 = ms[1];
+    }
+}
+
+// ---- the precise Halley pass, with F written at its A ------------------------------
+// e = 2^-(tau A log2 e) in double-float arithmetic (exp2_neg_precise), summed
+// in renormalised float pairs flushed to FP64, so g is known to ~1e-13 and
+// the pass may end the iteration (halley_update).  The same e, rounded to
+// FP32, is written as F (with its statistics when STATS).  A step from A to
+// A' = A + dA changes e^{-A tau} by at most |dA| tau e^{-min(A, A') tau} <=
+// |dA| / (e min(A, A')) (the maximum of tau e^{-x tau} is 1/(e x)), so when
+// the pass ends the iteration and that bound is <= kFluxShift, the F written
+// here is the final F (flux_ok) and no flux pass follows.
+constexpr double kFluxShift = 6e-8;   // ~1 FP32 ulp of F in [1/2, 1); the MUFU flux pass errs by ~1.2e-7
+
+template <bool STATS>
+__global__ void __launch_bounds__(kThreads, 4) mf_precise_kernel(const float* __restrict__ tau, long long n,
+                                                            MFState* st, Partial* part, float* __restrict__ F,
+                                                            StatPart* spart, StatsOut* sout)
+{
+    if (st->done) return;
+    __shared__ float2 tab[kExp2TabSize];
+    // one private 21-bin counter row per thread (21 is odd: conflict-free)
+    __shared__ unsigned int cnt[STATS ? kThreads * 21 : 1];
+    unsigned int* mine = cnt + (STATS ? threadIdx.x * 21 : 0);
+    if constexpr (STATS)
+        for (int k = 0; k < 21; ++k) mine[k] = 0;
+    load_exp2_table(tab);                             // ends with a barrier
+    const double A = st->A;
+    float a_hi, a_lo;
+    split_rate(A, a_hi, a_lo);
+    DFSum s0;                                         // sum e to ~1e-13 (float pairs, FP64)
+    // sum tau e (g' enters the step's certificate) and sum tau^2 e in FP32
+    // over a step of <= 32 values (nonnegative terms: <= 31 * 2^-24 relative),
+    // FP64 across steps; likewise the statistics
+    float s1 = 0.f, s2 = 0.f;
+    double sd1 = 0.0, sd2 = 0.0;
+    float m1 = 0.f, m2 = 0.f;
+    double md1 = 0.0, md2 = 0.0;
+    auto flush = [&] {
+        s0.flush();
+        sd1 += (double)s1;
+        sd2 += (double)s2;
+        s1 = 0.f;
+        s2 = 0.f;
+        if constexpr (STATS) {
+            md1 += (double)m1;
+            md2 += (double)m2;
+            m1 = 0.f;
+            m2 = 0.f;
+        }
+    };
+    auto proc = [&](float t) {
+        float eh, el;
+        exp2_neg_precise(t, a_hi, a_lo, tab, eh, el);
+        s0.add(eh, el);
+        const float te = t * eh;
+        s1 += te;
+        s2 = fmaf(t, te, s2);
+        // F: the pair rounded once; past the exponential's clamp (tau A log2 e
+        // > 100) the MUFU value, which flushes below 2^-126
+        const float y = t * a_hi;
+        const float f = y <= 100.f ? __fadd_rn(eh, el) : ex2(-y);
+        if constexpr (STATS) {
+            const float d = f - 0.5f;
+            m1 += d;
+            m2 = fmaf(d, d, m2);
+            mine[pdf_bin_unit(f)] += 1u;
+        }
+        return f;
+    };
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x, nthr = (long long)gridDim.x * blockDim.x;
+    if ((reinterpret_cast<uintptr_t>(tau) & 15) == 0 && (!F || (reinterpret_cast<uintptr_t>(F) & 15) == 0)) {
+        const float4* __restrict__ t4 = reinterpret_cast<const float4*>(tau);
+        float4* __restrict__ F4 = reinterpret_cast<float4*>(F);
+        const long long n4 = n >> 2;
+        long long i = tid;
+        // eight float4 in flight per thread, four with the statistics (their
+        // registers would otherwise push the kernel below four CTAs per SM)
+        constexpr int U = STATS ? 4 : 8;
+        for (; i + (U - 1) * nthr < n4; i += U * nthr) {
+            float4 v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) v[u] = t4[i + u * nthr];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                float4 o;
+                o.x = proc(v[u].x);
+                o.y = proc(v[u].y);
+                o.z = proc(v[u].z);
+                o.w = proc(v[u].w);
+                if (F) __stcs(F4 + i + u * nthr, o);
+            }
+            flush();                                  // at most 32 values per step
+        }
+        for (; i < n4; i += nthr) {
+            const float4 v = t4[i];
+            float4 o;
+            o.x = proc(v.x);
+            o.y = proc(v.y);
+            o.z = proc(v.z);
+            o.w = proc(v.w);
+            if (F) __stcs(F4 + i, o);
+            flush();
+        }
+        for (long long k = 4 * n4 + tid; k < n; k += nthr) {
+            const float f = proc(tau[k]);
+            if (F) F[k] = f;
+        }
+    } else {
+        int c = 0;
+        for (long long k = tid; k < n; k += nthr) {
+            const float f = proc(tau[k]);
+            if (F) F[k] = f;
+            if (++c == 32) {
+                flush();
+                c = 0;
+            }
+        }
+    }
+    flush();
+    __shared__ double sh[4][32];
+    double v[4] = {s0.value(), 0.0, sd1, sd2};
+    block_sum<4>(v, sh);                              // ends with a barrier
+    if constexpr (STATS) {
+        double ms[2] = {md1, md2};
+        block_sum<2>(ms, sh);
+        for (int k = threadIdx.x; k < 21; k += blockDim.x) {
+            unsigned int c = 0;
+            for (int r = 0; r < (int)blockDim.x; ++r) c += cnt[r * 21 + k];
+            spart[blockIdx.x].pdf[k] = c;
+        }
+        if (threadIdx.x == 0) {
+            spart[blockIdx.x].m1 = ms[0];
+            spart[blockIdx.x].m2 = ms[1];
+        }
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = Partial{v[0], v[1], v[2], v[3], 0, 0};
+    if (!last_block(&st->ticket)) return;
+    double tot[4];
+    partial_totals<4>(part, gridDim.x, tot, sh, [](const Partial& p, double (&x)[4]) {
+        x[0] = p.s0; x[1] = p.s0c; x[2] = p.s1; x[3] = p.s2;
+    });
+    __shared__ int s_final;
+    if (threadIdx.x == 0) {
+        halley_update(st, tot[0], tot[1], tot[2], tot[3], true);
+        const double An = st->A;
+        const double shift = fabs(An - A) / (2.718281828459045 * fmin(A, An));
+        st->flux_ok = st->done && st->status == LYA_OK && (An == A || shift <= kFluxShift);
+        s_final = st->flux_ok;
+    }
+    __syncthreads();
+    if (STATS && s_final) stats_totals(spart, sout, sh);
+}
+
+// ---- F = exp(-A tau) at the final A when the precise pass's F is not close
+//      enough to it, the convergence check at that A and, optionally, the
+//      statistics of that F (kept only when the check passes) ---------------
+
 template <bool STATS>
 __global__ void __launch_bounds__(kThreads) mf_flux_kernel(const float* __restrict__ tau, long long n,
                                                          MFState* st, Partial* part, float* __restrict__ F,
                                                          StatPart* spart, StatsOut* sout)
 {
-    if (st->done && st->status != LYA_OK) return;    // an error is final
+    // runs only after a precise pass ended the iteration without its own F
+    // being final (an error, or more passes to come, leaves it at once)
+    if (!st->done || st->status != LYA_OK || st->flux_ok) return;
     // one private 21-bin counter row per thread (21 is odd: conflict-free)
     __shared__ unsigned int cnt[STATS ? kThreads * 21 : 1];
     unsigned int* mine = cnt + (STATS ? threadIdx.x * 21 : 0);
@@ -300,22 +460,7 @@ __global__ void __launch_bounds__(kThreads) mf_flux_kernel(const float* __restri
             s_final = st->done && st->status == LYA_OK;
         }
         __syncthreads();
-        if (!s_final) return;
-        double ms[2] = {0.0, 0.0};
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-            ms[0] += spart[b].m1;
-            ms[1] += spart[b].m2;
-        }
-        block_sum<2>(ms, sh);
-        for (int k = threadIdx.x; k < 21; k += blockDim.x) {
-            unsigned long long c = 0;
-            for (int b = 0; b < (int)gridDim.x; ++b) c += spart[b].pdf[k];
-            sout->pdf[k] = c;
-        }
-        if (threadIdx.x == 0) {
-            sout->m1 = ms[0];
-            sout->m2 = ms[1];
-        }
+        if (s_final) stats_totals(spart, sout, sh);
     }
 }
 
@@ -501,12 +646,17 @@ static lya_status solve_on_scratch(const float* tau, int64_t n, double target, d
         err = cudaGetLastError();
     }
     for (int round = 0; err == cudaSuccess; ++round) {
-        // a fast (MUFU) Halley pass, a precise one, then the flux pass
-        mf_newton_kernel<false><<<grid, kThreads, 0, stream>>>(tau, n, st, part);
+        // a fast (MUFU) Halley pass, a precise one that writes F at its A, then
+        // the flux pass at the final A, which leaves at once when the precise
+        // pass's F is final
+        mf_newton_kernel<<<grid, kThreads, 0, stream>>>(tau, n, st, part);
         count_launch();
         err = cudaGetLastError();
         if (err == cudaSuccess) {
-            mf_newton_kernel<true><<<grid, kThreads, 0, stream>>>(tau, n, st, part);
+            if (spart)
+                mf_precise_kernel<true><<<grid, kThreads, 0, stream>>>(tau, n, st, part, flux_out, spart, sout);
+            else
+                mf_precise_kernel<false><<<grid, kThreads, 0, stream>>>(tau, n, st, part, flux_out, nullptr, nullptr);
             count_launch();
             err = cudaGetLastError();
         }
@@ -725,19 +875,25 @@ __global__ void __launch_bounds__(kThreads) mf_sums_kernel(const float* __restri
     float a_hi, a_lo;
     split_rate(A, a_hi, a_lo);
     DFSum s0;                                   // sum e precise (double-float exponentials)
-    KahanF32 s1;
-    float s2 = 0.f;
+    float s1 = 0.f, s2 = 0.f;                   // as the precise pass: FP32 per step, FP64 across
+    double sd1 = 0.0, sd2 = 0.0;
     stream_f32_steps(tau, n, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x,
                      [&](float t) {
         float eh, el;
         exp2_neg_precise(t, a_hi, a_lo, tab, eh, el);
         s0.add(eh, el);
         const float te = t * eh;
-        s1.add(te);
+        s1 += te;
         s2 = fmaf(t, te, s2);
-    }, [&] { s0.flush(); });
+    }, [&] {
+        s0.flush();
+        sd1 += (double)s1;
+        sd2 += (double)s2;
+        s1 = 0.f;
+        s2 = 0.f;
+    });
     __shared__ double sh[4][32];
-    double v[4] = {s0.value(), 0.0, (double)s1.s - (double)s1.c, (double)s2};
+    double v[4] = {s0.value(), 0.0, sd1, sd2};
     block_sum<4>(v, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = Partial{v[0], v[1], v[2], v[3], 0, 0};
     if (!last_block(&out->ticket)) return;

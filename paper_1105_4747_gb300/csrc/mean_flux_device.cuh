@@ -58,7 +58,7 @@ __device__ __forceinline__ void stream_f32(const float* __restrict__ x, long lon
 }
 
 // stream_f32 with done() called after every step of at most 32 values per
-// thread (the fixed-point sums move their integer part into FP64 there).
+// thread (the per-thread FP32 or float-pair sums move into FP64 there).
 template <typename Fn, typename Done>
 __device__ __forceinline__ void stream_f32_steps(const float* __restrict__ x, long long n, long long tid,
                                                  long long nthr, Fn&& f, Done&& done)
@@ -108,6 +108,8 @@ struct MFState {
     int iter, max_iter, done, status;   // status: LYA_OK / LYA_EINVAL / LYA_ENOCONV (not yet converged)
     unsigned int ticket;
     unsigned int tau_max_bits;          // largest tau (float bits; tau >= 0 orders like its bits)
+    int flux_ok;                        // the precise pass's F is the final F (no flux pass needed)
+    int flux_pad;
     unsigned long long hist[kHistBins + 1];   // + sampled zeros
 };
 
@@ -245,6 +247,18 @@ __device__ __forceinline__ void exp_neg(float t, float a_hi, float a_lo, float& 
 // error grows as ~1.5e-15 y^2 (the series omits the higher terms of u_lo ~
 // y_lo ln 2) on values that shrink as 2^-y.
 constexpr float kLn2Hi = 0x1.62e430p-1f;                 // float nearest ln 2
+
+// x rounded to the nearest integer (ties to even), as a float and as an int,
+// for |x| < 2^22: adding 1.5 * 2^23 leaves that integer in the low bits of
+// the sum (its ulp is 1), all on the FMA and integer pipes (rintf and the
+// float-to-int conversion would use the quarter-rate conversion unit).
+__device__ __forceinline__ float round_to_int(float x, int& n)
+{
+    constexpr float kShift = 0x1.8p23f;
+    const float s = __fadd_rn(x, kShift);
+    n = __float_as_int(s) - __float_as_int(kShift);
+    return __fsub_rn(s, kShift);
+}
 constexpr float kLn2Lo = -0x1.05c610p-29f;               // ln 2 - kLn2Hi, to float
 
 // Copies kExp2Tab into shared memory (whole block; ends with a barrier).
@@ -261,8 +275,8 @@ __device__ __forceinline__ void exp2_neg_precise(float t, float a_hi, float a_lo
     const float y_raw = t * a_hi;
     const float y_hi = fminf(y_raw, 100.f);
     const float y_lo = y_raw <= 100.f ? fmaf(t, a_lo, fmaf(t, a_hi, -y_hi)) : 0.f;
-    const float Nf = rintf(y_hi * 1024.f);
-    const int N = (int)Nf;
+    int N;
+    const float Nf = round_to_int(y_hi * 1024.f, N);
     const float r = fmaf(Nf, -1.f / 1024.f, y_hi);                     // exact
     const float u_hi = -r * kLn2Hi;
     const float u_lo = fmaf(-r, kLn2Hi, -u_hi) - fmaf(r, kLn2Lo, y_lo * kLn2Hi);
@@ -278,6 +292,31 @@ __device__ __forceinline__ void exp2_neg_precise(float t, float a_hi, float a_lo
     const float scale = __int_as_float((127 - (N >> 10)) << 23);        // 2^-(N >> 10), exact
     e_hi = R_hi * scale;
     e_lo = R_lo * scale;
+}
+
+// e = 2^-y for the fast pass on the FMA pipe: y = n + r with n the nearest
+// integer (round_to_int), 2^-y = 2^-n 2^f with f = (n - y_hi) - y_lo in
+// [-1/2, 1/2] (up to y_lo), 2^f by a degree-6 polynomial fitted by least
+// squares on Chebyshev nodes (exp2_poly_fit.py beside this file, degree 6):
+// within ~8e-8 of 2^f in FP32 and ~1e-9 on average over f, where the MUFU
+// ex2 errs by a few ulp the same way for neighbouring arguments.  y is
+// clamped at 100 like exp2_neg_precise.
+__device__ __forceinline__ float exp2_neg_fast(float t, float a_hi, float a_lo)
+{
+    const float y_raw = t * a_hi;
+    const float y_hi = fminf(y_raw, 100.f);
+    const float y_lo = y_raw <= 100.f ? fmaf(t, a_lo, fmaf(t, a_hi, -y_hi)) : 0.f;
+    int n;
+    const float nf = round_to_int(y_hi, n);
+    const float f = (nf - y_hi) - y_lo;
+    float p = 0x1.446c7ep-13f;
+    p = fmaf(p, f, 0x1.5f48c8p-10f);
+    p = fmaf(p, f, 0x1.3b29d8p-7f);
+    p = fmaf(p, f, 0x1.c6aeccp-5f);
+    p = fmaf(p, f, 0x1.ebfbe0p-3f);
+    p = fmaf(p, f, 0x1.62e430p-1f);
+    p = fmaf(p, f, 0x1p+0f);
+    return p * __int_as_float((127 - n) << 23);                         // 2^-n, n <= 100: exact
 }
 
 // Per-thread sum of e_hi + e_lo values: a float pair (h, l) with |l| <=
@@ -313,10 +352,23 @@ __device__ __forceinline__ int pdf_bin(float F)
 {
     if (!(F == F)) return 0;
     const float f = fminf(fmaxf(F, -1.f), 2.f);
-    int k = (int)floorf(fmaf(f, 20.f, 0.5f));
-    if (fmaf(f, 40.f, -(float)(2 * k - 1)) < 0.f) k -= 1;
-    else if (fmaf(f, 40.f, -(float)(2 * k + 1)) >= 0.f) k += 1;
+    int k;
+    const float kf = round_to_int(20.f * f, k);          // the nearest bin, or a neighbour of it
+    if (fmaf(f, 40.f, -fmaf(2.f, kf, -1.f)) < 0.f) k -= 1;
+    else if (fmaf(f, 40.f, -fmaf(2.f, kf, 1.f)) >= 0.f) k += 1;
     return min(max(k, 0), 20);
+}
+
+// pdf_bin for F in [0, 1] (a flux the root-find just formed): the bin is the
+// nearest integer to 20 F, decided exactly by pdf_bin only when 20 F (one
+// rounding, <= 2^-20 off) lies within 2^-18 of a bin edge k + 1/2.
+__device__ __forceinline__ int pdf_bin_unit(float F)
+{
+    const float p = 20.f * F;
+    int k;
+    const float kf = round_to_int(p, k);
+    if (fabsf(p - kf) >= 0.5f - 0x1p-18f) k = pdf_bin(F);
+    return k;
 }
 
 
@@ -383,7 +435,8 @@ constexpr double kApproxGErr = 1e-6;
 // Bounds used by the precise pass's certificate: on the error of its g
 // (double-float exponentials, ~3e-14 per term at worst; float-pair partial
 // sums of at most 32 terms, ~1e-13 relative at worst; FP64 beyond) and on
-// the relative error of its g' (compensated FP32 per thread, FP64 beyond).
+// the relative error of its g' (FP32 products and sums of at most 32
+// nonnegative terms, ~2e-6 at worst, or compensated FP32; FP64 beyond).
 constexpr double kPreciseGErr = 2e-13;
 constexpr double kSlopeRelErr = 1e-5;
 
