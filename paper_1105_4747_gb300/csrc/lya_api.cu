@@ -151,9 +151,10 @@ lya_status make_tau_launch(lya_field f, const lya_extract_params* p, TauLaunch* 
         return LYA_EINVAL;
     const int N = (int)f->desc.n_pix;
     const Physics ph = physics(f->desc, p->gamma12);
-    // |v_pec| < c is checked per value; keep |v_pec|/du below 2^29 pixels so the
-    // kernels' target-pixel arithmetic stays in 32-bit integers
-    if (!(ph.du > 2.99792458e5 / 536870912.0)) return LYA_EINVAL;
+    // |v_pec| < c is checked per value; keep |v_pec|/du below 2^22 pixels so the
+    // kernels round v/du to whole pixels exactly with the 1.5 * 2^23 shifter
+    // (pixels narrower than 0.0715 km/s are refused)
+    if (!(ph.du > 2.99792458e5 / 4194304.0)) return LYA_EINVAL;
 
     // Largest temperature any source can have -> bound on the window half-width
     // (pixels) of every line: nsigma b(T_max)/du + 1/2 (the residual), +1 margin.

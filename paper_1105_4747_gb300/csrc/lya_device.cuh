@@ -21,6 +21,18 @@ __device__ __forceinline__ float ex2(float x)
     return y;
 }
 
+// x rounded to the nearest integer (ties to even), as a float and as an int,
+// for |x| < 2^22: adding 1.5 * 2^23 leaves that integer in the low bits of
+// the sum (its ulp is 1), all on the FMA and integer pipes (rintf and the
+// float-to-int conversion would use the quarter-rate conversion unit).
+__device__ __forceinline__ float round_to_int(float x, int& n)
+{
+    constexpr float kShift = 0x1.8p23f;
+    const float s = __fadd_rn(x, kShift);
+    n = __float_as_int(s) - __float_as_int(kShift);
+    return __fsub_rn(s, kShift);
+}
+
 // log2(x) on the MUFU unit (PTX lg2.approx.ftz.f32; x is a normal positive
 // temperature or density here).
 __device__ __forceinline__ float lg2(float x)

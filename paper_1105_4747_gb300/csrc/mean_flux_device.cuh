@@ -248,17 +248,6 @@ __device__ __forceinline__ void exp_neg(float t, float a_hi, float a_lo, float& 
 // y_lo ln 2) on values that shrink as 2^-y.
 constexpr float kLn2Hi = 0x1.62e430p-1f;                 // float nearest ln 2
 
-// x rounded to the nearest integer (ties to even), as a float and as an int,
-// for |x| < 2^22: adding 1.5 * 2^23 leaves that integer in the low bits of
-// the sum (its ulp is 1), all on the FMA and integer pipes (rintf and the
-// float-to-int conversion would use the quarter-rate conversion unit).
-__device__ __forceinline__ float round_to_int(float x, int& n)
-{
-    constexpr float kShift = 0x1.8p23f;
-    const float s = __fadd_rn(x, kShift);
-    n = __float_as_int(s) - __float_as_int(kShift);
-    return __fsub_rn(s, kShift);
-}
 constexpr float kLn2Lo = -0x1.05c610p-29f;               // ln 2 - kLn2Hi, to float
 
 // Copies kExp2Tab into shared memory (whole block; ends with a barrier).

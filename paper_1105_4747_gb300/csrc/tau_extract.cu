@@ -78,7 +78,7 @@ template <> struct Prec<LYA_PREC_F64> {
     __device__ static double value(const Acc& a) { return a.s; }
 };
 
-// x mod N in [0, N) for |x| < 2^30 (the host bounds |v_pec|/du below 2^29);
+// x mod N in [0, N) for |x| < 2^30 (the host bounds |v_pec|/du below 2^22);
 // one wrap either way is a compare and an add, farther ones a division.
 __device__ __forceinline__ int wrap_pixel(int x, int N)
 {
@@ -97,9 +97,11 @@ __device__ __forceinline__ int wrap_pixel(int x, int N)
 // exponential 2^(lw - x^2), its argument one FFMA.
 struct SrcF32 { float a, bb, lw; int t, h; };
 
-__device__ __forceinline__ float target_shift_f32(float v, const TauLaunch& L)
+// The source's shift in whole pixels, round(v / du), as a float and an int
+// (|v| / du < 2^22, which the host checks).
+__device__ __forceinline__ float target_shift_f32(float v, const TauLaunch& L, int& isf)
 {
-    return rintf(v * L.inv_du);
+    return round_to_int(v * L.inv_du, isf);
 }
 
 __device__ __forceinline__ SrcF32 prep_f32(const TauLaunch& L, float rho, float v, float T, int j)
@@ -110,10 +112,11 @@ __device__ __forceinline__ SrcF32 prep_f32(const TauLaunch& L, float rho, float 
     const float lt = L.t_mode != 0 ? fmaf(L.gm1, fminf(lr, L.lpivot), L.lT0) : lg2(T) - kLog2_1e4;
     s.lw = fmaf(-1.2f, lt, 2.f * lr);
     const float c = L.c_coef * ex2(-0.5f * lt);          // sqrt(log2 e) / b
-    const float sf = target_shift_f32(v, L);
+    int isf;
+    const float sf = target_shift_f32(v, L, isf);
     float r = fmaf(-sf, L.du_hi, v);                     // exact product inside the fma
     r = fmaf(-sf, L.du_lo, r);
-    s.t = wrap_pixel(j + (int)sf, L.n_pix);
+    s.t = wrap_pixel(j + isf, L.n_pix);
     s.a = c * L.du_hi;
     s.bb = c * r;
     // |m du - r| <= nsigma b needs |m| <= (nsigma b + |r|)/du, and nsigma b/du =
@@ -206,7 +209,11 @@ __global__ void __launch_bounds__(512) tau_kernel(const TauLaunch L)
             const float v = vpec[j];
             int t;
             if (PREC == LYA_PREC_F64) t = wrap_pixel(j + (int)rint((double)v * L.inv_du_d), N);
-            else t = wrap_pixel(j + (int)target_shift_f32(v, L), N);
+            else {
+                int isf;
+                (void)target_shift_f32(v, L, isf);
+                t = wrap_pixel(j + isf, N);
+            }
             atomicAdd(&bin[t + 1], 1);
         }
     }
