@@ -23,7 +23,8 @@
 // Per source (FP32, MUFU):  T_j = stored or T0 min(rho_j, pivot)^(gamma-1)
 //   w_j = rho_j^2 (T_j/1e4)^-1.2          (n_HI / b of Eq. 4 and Eq. 6 up to K)
 //   c_j = sqrt(log2 e) / b_j,  a_j = c_j du,   so exp(-(d/b)^2) = 2^-(c d)^2.
-// Per pair: x = fma(m, a_j, -c_j r_j); tau += w_j * ex2(-x*x).
+// Per pair: x = fma(m, a_j, -c_j r_j); tau += ex2(lw_j - x*x), lw_j = log2 w_j
+// (the pixel-averaged profile: w_j times a difference of two erfc).
 #include <algorithm>
 #include <cfloat>
 #include <cstdint>
@@ -751,13 +752,32 @@ __device__ __forceinline__ void wrap_segment(const float4* __restrict__ rec, int
     }
 }
 
+// A lane's finished pixels o .. o + NPX - 1 of tau, written straight to HBM
+// (no staging in shared memory): one 8- or 16-byte streaming store where the
+// row allows it (al: the row pointer is aligned to NPX floats).
+template <int NPX>
+__device__ __forceinline__ void store_pixels(float* out, int o, int N, bool al, const float (&t)[NPX])
+{
+    if (al && o + NPX <= N) {
+        if constexpr (NPX == 4)
+            __stcs(reinterpret_cast<float4*>(out + o), make_float4(t[0], t[1], t[2], t[3]));
+        else
+            __stcs(reinterpret_cast<float2*>(out + o), make_float2(t[0], t[1]));
+        return;
+    }
+#pragma unroll
+    for (int m = 0; m < NPX; ++m)
+        if (o + m < N) out[o + m] = t[m];
+}
+
 // Step 7 with two lanes per tile, four pixels each, over the tiles in order.
 template <bool COMP, bool AVG, int EXP>
 __device__ __forceinline__ void tiles_by_four(const float4* __restrict__ rec, const int* bin, const short* Lt,
                                               const short* Rt, const short* order, const short* ok0,
                                               const short* ok1, bool ext, int N, int NT, float K,
-                                              float* tau_s, int tid, int nt, int base, int nsrc)
+                                              float* out, int tid, int nt, int base, int nsrc)
 {
+    const bool al16 = (reinterpret_cast<uintptr_t>(out) & 15) == 0;
     const int half = tid & 1, ng = nt / 2, grp = tid / 2;
     for (int round = 0; round * ng < NT; ++round) {
         const int i = round * ng + ((round & 1) ? ng - 1 - grp : grp);
@@ -775,9 +795,10 @@ __device__ __forceinline__ void tiles_by_four(const float4* __restrict__ rec, co
                 pair4_segment<COMP, AVG, EXP>(rec, k0, k1, (float)o + shift, S, C);
             });
         }
+        float t[4];
 #pragma unroll
-        for (int m = 0; m < 4; ++m)
-            if (o + m < N) tau_s[o + m] = K * (COMP ? __fsub_rn(S[m], C[m]) : S[m]);
+        for (int m = 0; m < 4; ++m) t[m] = K * (COMP ? __fsub_rn(S[m], C[m]) : S[m]);
+        store_pixels<4>(out, o, N, al16, t);
     }
 }
 
@@ -808,8 +829,7 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
     int* cnt = reinterpret_cast<int*>(rec + round_up4(N + Cx)) + 4;   // N (padded to 4), cnt[-1] = 0
     int* bin = cnt - 1;                                          // after the scatter: bin[t] = start(t),
                                                                  // bin[t + 1] = end(t)
-    int* reach = cnt + round_up4(N);                         // NE; tau once the runs are known
-    float* tau_s = reinterpret_cast<float*>(reach);
+    int* reach = cnt + round_up4(N);                         // NE
     short* Lt = reinterpret_cast<short*>(reach + NE);        // NT
     short* Rt = Lt + NT;                                     // NT
     short* order = Rt + NT;                                  // NT: tiles by candidate count
@@ -1097,23 +1117,23 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
 
     // 7. lane groups walk the tiles in that order (reversed on alternate
     //    rounds, so every warp's total work evens out); each lane owns two
-    //    adjacent pixels, or four where the runs are long; tau goes to shared
-    //    memory (the reach array is free)
+    //    adjacent pixels, or four where the runs are long, and writes them
+    //    to HBM itself (store_pixels: no staging, no final barrier)
     const float K = L.K;
     if (ALT_EXP && L.exp_method != LYA_EXP_MUFU) {
         if constexpr (ALT_EXP && !AVG) {
             if (L.exp_method == LYA_EXP_RECURRENCE)
                 tiles_by_four<COMP, false, LYA_EXP_RECURRENCE>(rec, bin, Lt, Rt, order, ok0, ok1, ext, N, NT, K,
-                                                               tau_s, tid, nt, base, nsrc);
+                                                               out, tid, nt, base, nsrc);
             else
                 tiles_by_four<COMP, false, LYA_EXP_POLY_SPLIT>(rec, bin, Lt, Rt, order, ok0, ok1, ext, N, NT, K,
-                                                               tau_s, tid, nt, base, nsrc);
+                                                               out, tid, nt, base, nsrc);
         }
-        g.sync();
     } else if (warp_tot[kRunTotal] >= kLongRun * NT) {
-        tiles_by_four<COMP, AVG, LYA_EXP_MUFU>(rec, bin, Lt, Rt, order, ok0, ok1, ext, N, NT, K, tau_s, tid, nt, base, nsrc);
-        g.sync();
+        tiles_by_four<COMP, AVG, LYA_EXP_MUFU>(rec, bin, Lt, Rt, order, ok0, ok1, ext, N, NT, K, out, tid, nt, base,
+                                               nsrc);
     } else {
+    const bool al8 = (reinterpret_cast<uintptr_t>(out) & 7) == 0;
     const int lane_q = tid & (kLanesPerTile - 1);
     const int npairs = nt / kLanesPerTile, pair = tid / kLanesPerTile;
     for (int round = 0; round * npairs < NT; ++round) {
@@ -1139,18 +1159,9 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
                 pair2_segment<COMP, AVG, FOLD>(rec, k0, k1, (float)o + shift, S, C);
             });
         }
-        if (o < N) tau_s[o] = K * (COMP ? __fsub_rn(S[0], C[0]) : S[0]);
-        if (o + 1 < N) tau_s[o + 1] = K * (COMP ? __fsub_rn(S[1], C[1]) : S[1]);
+        const float t[2] = {K * (COMP ? __fsub_rn(S[0], C[0]) : S[0]), K * (COMP ? __fsub_rn(S[1], C[1]) : S[1])};
+        store_pixels<2>(out, o, N, al8, t);
     }
-    g.sync();
-    }
-
-    // 8. tau to HBM in order
-    if (vec && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
-        for (int k = tid; 4 * k < N; k += nt)
-            reinterpret_cast<float4*>(out)[k] = reinterpret_cast<const float4*>(tau_s)[k];
-    } else {
-        for (int i = tid; i < N; i += nt) out[i] = tau_s[i];
     }
 }
 
