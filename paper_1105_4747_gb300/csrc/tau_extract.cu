@@ -1026,7 +1026,7 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
 
     // 6. tiles ordered by candidate count, largest first (counting sort)
     constexpr int kMaxTilesPerThread = (MAXQ + kTile - 1) / kTile;   // NT <= MAXQ nt / kTile
-    int tkey[kMaxTilesPerThread], kk0[kMaxTilesPerThread], kk1[kMaxTilesPerThread];
+    int tkey[kMaxTilesPerThread], trank[kMaxTilesPerThread], kk0[kMaxTilesPerThread], kk1[kMaxTilesPerThread];
     bool wrap[kMaxTilesPerThread];
     int runs = 0;
 #pragma unroll
@@ -1067,7 +1067,7 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
                 for_tile_run(bin, N, lx, rx, [&](int k0, int k1, float) { c += k1 - k0; });
             }
             tkey[u] = kTileKeys - 1 - min(c, kTileKeys - 1);
-            atomicAdd(&tile_hist[tkey[u]], 1);
+            trank[u] = atomicAdd(&tile_hist[tkey[u]], 1);    // its rank among the tiles of its key
             runs += c;
         }
     }
@@ -1105,7 +1105,7 @@ __device__ __forceinline__ void tile_skewer(const TauLaunch& L, const float* __r
     for (int u = 0; u < kMaxTilesPerThread; ++u) {
         if (tkey[u] < 0) continue;
         LYA_BOUND(tkey[u] < kTileKeys);
-        const int pos = atomicAdd(&tile_hist[tkey[u]], 1);
+        const int pos = tile_hist[tkey[u]] + trank[u];     // the key's first slot + the rank
         LYA_BOUND(pos >= 0 && pos < NT);
         order[pos] = (short)((tid + u * nt) | (wrap[u] ? kWrapTile : 0));
         if (ext && !wrap[u]) {
