@@ -45,15 +45,15 @@ ALG_BYTES_PER_PX = 16          # rho, vpec, T read (12 B) + tau written (4 B)
 # scaled by the number of skewers, with the SHA-1 of the kernel source each
 # was taken on: reported as null once paper_1105_4747_gb300/csrc/tau_extract.cu
 # differs from it.
-TAU_DRAM_PROFILE = {"gpc": ((402.785536e6 + 84.164096e6) / 8192, "3672f7192d5423a42bd2f3781912f2c59aa8f3af"),
-                    "grid1536": ((2.416239e9 + 0.755802112e9) / 131072, "3672f7192d5423a42bd2f3781912f2c59aa8f3af")}
+TAU_DRAM_PROFILE = {"gpc": ((402.951168e6 + 112.1984e6) / 8192, "88b1ac9fac8321f603415f16357f49a982d64067"),
+                    "grid1536": ((2.416071936e9 + 0.759599616e9) / 131072, "88b1ac9fac8321f603415f16357f49a982d64067")}
 
 
 # ncu pipe utilisation of the same tau-kernel launch as TAU_DRAM_PROFILE["gpc"]
 # (8,192 skewers, --set full, profiles/tau_tile_kernel_gpc_8192x4096.md), with
 # the code hash it was taken on: reported as null once the kernel differs.
-TAU_PIPE_PROFILE = {"gpc": ({"fma_pct": 20.2, "xu_pct": 20.3, "alu_pct": 44.4, "lsu_pct": 18.4,
-                             "issue_active_pct": 65.0}, "3672f7192d5423a42bd2f3781912f2c59aa8f3af")}
+TAU_PIPE_PROFILE = {"gpc": ({"fma_pct": 19.4, "xu_pct": 20.4, "alu_pct": 46.1, "lsu_pct": 19.3,
+                             "issue_active_pct": 67.6}, "88b1ac9fac8321f603415f16357f49a982d64067")}
 FP32_OPS_PER_PAIR = 6          # per pair of the sum: argument (2), square, exponent scale, weight, add
 KB_J_PER_K = 1.380649e-23
 M_H_KG = 1.6735575e-27
