@@ -12,10 +12,10 @@
 // and updates A in device memory, so passes chain on the stream without a
 // host round trip.  A pass launched after convergence returns at once.
 //
-// Precision: the first Halley pass of a round uses the MUFU exponential of a
-// double-float argument y = tau A log2(e) = y_hi + y_lo, e = 2^-y_hi (1 - y_lo
-// ln 2), summed in compensated FP32 (g to ~1e-7: a fast start that never ends
-// the iteration).  The second Halley pass forms e in double-float arithmetic
+// Precision: the first Halley pass of a round forms e = 2^-y, y = tau A log2(e)
+// = y_hi + y_lo (a double-float argument), with an FP32 polynomial on the FMA
+// pipe, summed in FP32 steps and FP64 across them (g to ~1e-9: a fast start
+// that never ends the iteration).  The second Halley pass forms e in double-float arithmetic
 // to ~3e-14 (exp2_neg_precise) and sums it in renormalised float pairs
 // flushed to FP64 every 32 values, so g is known to ~1e-13; it ends the
 // iteration when |g| <= tol (1e-12) or when its Newton step is certified to
