@@ -14,7 +14,7 @@ from __future__ import annotations
 
 import numpy as np
 
-DEGREE = 8
+DEGREE = 6
 P_SCALE = 0.4
 X_MAX = 10.0
 NODES = 400

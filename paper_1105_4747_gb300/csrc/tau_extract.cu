@@ -462,23 +462,21 @@ __device__ __forceinline__ void kahan_fold(float& S, float& C, float P)
 }
 
 // erfc(x) for x >= 0 in FP32 (the pixel-averaged profile): t = 1/(1 + 0.4 x)
-// and erfc(x) = t 2^(P(t) - x^2 log2 e), P a degree-8 polynomial fitted by
+// and erfc(x) = t 2^(P(t) - x^2 log2 e), P a degree-6 polynomial fitted by
 // least squares on Chebyshev nodes of t (erfc_fit.py beside this file): within
-// ~1.4e-6 of erfc for x < 4 and ~6e-6 out to x = 9, where the rounding of
-// x^2 log2 e sets it; two MUFU and ten FMA-pipe operations.  Below 2^-126 the
-// result flushes to zero.
+// ~3e-6 of erfc for x < 4 and ~7e-6 out to x = 9, where the rounding of
+// x^2 log2 e sets it; two MUFU and eight FMA-pipe operations.  Below 2^-126
+// the result flushes to zero.
 __device__ __forceinline__ float erfc_pos(float x)
 {
     const float t = rcp_approx(fmaf(0.4f, x, 1.f));
-    float p = -0x1.3a4214p-2f;
-    p = fmaf(p, t, 0x1.5eeeb8p+0f);
-    p = fmaf(p, t, -0x1.1c3026p+1f);
-    p = fmaf(p, t, 0x1.8762c2p+0f);
-    p = fmaf(p, t, -0x1.6656a4p-1f);
-    p = fmaf(p, t, 0x1.d5c156p-2f);
-    p = fmaf(p, t, 0x1.24043ep-1f);
-    p = fmaf(p, t, 0x1.722eep+0f);
-    p = fmaf(p, t, -0x1.12eb56p+1f);
+    float p = 0x1.61e06ap-2f;
+    p = fmaf(p, t, -0x1.15daap+0f);
+    p = fmaf(p, t, 0x1.c0d2bap-1f);
+    p = fmaf(p, t, -0x1.d295c4p-4f);
+    p = fmaf(p, t, 0x1.624c58p-1f);
+    p = fmaf(p, t, 0x1.6ea9f6p+0f);
+    p = fmaf(p, t, -0x1.12d6acp+1f);
     return t * ex2(fmaf(-x * 1.44269504f, x, p));
 }
 

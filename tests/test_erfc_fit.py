@@ -32,7 +32,7 @@ def test_kernel_uses_the_fitted_coefficients():
     fit = _fit()
     body = _kernel_body()
     lits = [float.fromhex(h) for h in re.findall(r"(-?0x[0-9a-f.]+p[-+]?\d+)f", body)]
-    # c8 .. c0 in Horner order
+    # c6 .. c0 in Horner order
     np.testing.assert_array_equal(np.array(lits[::-1], dtype=np.float32), fit.coefficients())
     assert "fmaf(0.4f, x, 1.f)" in body and fit.P_SCALE == 0.4
 
@@ -45,7 +45,7 @@ def test_error_bound():
     got = fit.erfc_reference(x).astype(np.float64)
     ref = erfc(x.astype(np.float64))
     rel = np.abs(got / ref - 1.0)
-    assert float(rel[x < 4].max()) < 2e-6
+    assert float(rel[x < 4].max()) < 4e-6
     assert float(rel.max()) < 1e-5
     # the cell differences of the averaged profile: erfc(a) - erfc(a + h) for
     # cells down to a fiftieth of a line width keep their relative accuracy
@@ -59,7 +59,7 @@ def test_error_bound():
 def test_special_values():
     pytest.importorskip("scipy")
     fit = _fit()
-    assert float(fit.erfc_reference(np.float32([0.0]))[0]) == pytest.approx(1.0, abs=5e-7)
+    assert float(fit.erfc_reference(np.float32([0.0]))[0]) == pytest.approx(1.0, abs=4e-6)
     # far wing: tiny and positive, monotone
     v = fit.erfc_reference(np.linspace(0, 9, 1001).astype(np.float32)).astype(np.float64)
     assert np.all(np.diff(v) < 0) and np.all(v > 0)
