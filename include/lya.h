@@ -519,6 +519,19 @@ const char* lya_strerror(lya_status status);
  */
 uint64_t lya_kernel_launches(void);
 
+/*
+ * Used-memory high watermark (bytes) of the memory pool the library draws its
+ * per-call scratch from on the current device (diagnostics: the allocating
+ * calls' root-find state, partials and statistics buffers come from it; the
+ * no-alloc root-find takes nothing from it).  The pool is the library's own,
+ * created at first use with its release threshold at the maximum, so its
+ * memory stays mapped between calls; the caller's pools are not touched.
+ * reset != 0 resets the watermark to the memory currently in use, after
+ * reading it into *bytes when bytes is not NULL.  LYA_EINVAL: bytes NULL and
+ * reset 0; LYA_ECUDA: the pool could not be created.
+ */
+lya_status lya_scratch_high_watermark(int reset, uint64_t* bytes);
+
 /* Version string of the library build. */
 const char* lya_version(void);
 

@@ -40,6 +40,7 @@ from ._binding import (  # noqa: F401
     rescale_mean_flux_sharded,
     tau_moments,
     kernel_launches,
+    scratch_high_watermark,
     library_path,
     load_library,
     rescale_mean_flux,

@@ -105,6 +105,15 @@ def kernel_launches() -> int:
     return int(load_library().lya_kernel_launches())
 
 
+def scratch_high_watermark(reset: bool = False) -> int:
+    """Used-memory high watermark (bytes) of the library's scratch pool on the
+    current device, then reset it if asked (lya_scratch_high_watermark)."""
+    v = ctypes.c_uint64(0)
+    _check(load_library().lya_scratch_high_watermark(1 if reset else 0, ctypes.byref(v)),
+           "lya_scratch_high_watermark")
+    return int(v.value)
+
+
 def library_path() -> str:
     return _LIB_PATH
 
@@ -126,6 +135,7 @@ def load_library():
         lib.lya_version.restype = ctypes.c_char_p
         lib.lya_kernel_launches.argtypes = []
         lib.lya_kernel_launches.restype = ctypes.c_uint64
+        lib.lya_scratch_high_watermark.argtypes = [i32, ctypes.POINTER(ctypes.c_uint64)]
         lib.lya_create_field.argtypes = [ctypes.POINTER(_FieldDesc), vp, vp, vp, i32, vp, ctypes.POINTER(vp)]
         lib.lya_field_load.argtypes = [vp, vp, vp, vp, i32, vp]
         lib.lya_destroy_field.argtypes = [vp]

@@ -251,10 +251,10 @@ lya_status flux_power_3d_run(const float* flux, const int* cells_host, int64_t n
     int* cell = nullptr;
     float2* planes = nullptr;
     const size_t nd = 1 + (size_t)H + 4 * (size_t)n_shells + grid_sum;
-    cudaError_t e = cudaMallocAsync((void**)&d, sizeof(double) * nd, stream);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&ticket, sizeof(unsigned int), stream);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&cell, sizeof(int) * (size_t)n_los, stream);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&planes, sizeof(float2) * (size_t)H * cells, stream);
+    cudaError_t e = scratch_malloc((void**)&d, sizeof(double) * nd, stream);
+    if (e == cudaSuccess) e = scratch_malloc((void**)&ticket, sizeof(unsigned int), stream);
+    if (e == cudaSuccess) e = scratch_malloc((void**)&cell, sizeof(int) * (size_t)n_los, stream);
+    if (e == cudaSuccess) e = scratch_malloc((void**)&planes, sizeof(float2) * (size_t)H * cells, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, sizeof(double) * (1 + H + 4 * (size_t)n_shells), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ticket, 0, sizeof(unsigned int), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(planes, 0, sizeof(float2) * (size_t)H * cells, stream);
@@ -279,7 +279,7 @@ lya_status flux_power_3d_run(const float* flux, const int* cells_host, int64_t n
         }
     }
     short* order = nullptr;
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&order, sizeof(short) * (size_t)cells, stream);
+    if (e == cudaSuccess) e = scratch_malloc((void**)&order, sizeof(short) * (size_t)cells, stream);
     if (e == cudaSuccess) {
         const size_t smem_keys = sizeof(int) * (2 * (size_t)(n_perp / 2) * (n_perp / 2) + 2);
         f3_order_kernel<<<1, kPlaneThreads, smem_keys, stream>>>(n_perp, order);

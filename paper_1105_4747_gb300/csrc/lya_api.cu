@@ -234,6 +234,24 @@ const char* lya_version(void) { return "lya 0.1 (sm_103a)"; }
 
 uint64_t lya_kernel_launches(void) { return lya::launches_so_far(); }
 
+lya_status lya_scratch_high_watermark(int reset, uint64_t* bytes)
+{
+    if (!bytes && !reset) return LYA_EINVAL;
+    cudaMemPool_t pool = lya::scratch_pool();
+    if (!pool) return LYA_ECUDA;
+    if (bytes) {
+        unsigned long long v = 0;
+        const cudaError_t e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &v);
+        if (e != cudaSuccess) return from_cuda(e);
+        *bytes = (uint64_t)v;
+    }
+    if (reset) {
+        unsigned long long zero = 0;
+        return from_cuda(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero));
+    }
+    return LYA_OK;
+}
+
 lya_status lya_create_field(const lya_field_desc* desc, const float* rho, const float* vpec,
                             const float* temp, int src, void* stream, lya_field* out)
 {

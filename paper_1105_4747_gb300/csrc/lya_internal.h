@@ -159,4 +159,15 @@ uint64_t launches_so_far();
 // Number of SMs of the current device (cached).
 int sm_count();
 
+// Stream-ordered scratch for the library's per-call buffers (root-find state
+// and partials, statistics, transforms), from a memory pool the library owns
+// on the current device, created at first use with its release threshold at
+// the maximum: its memory stays mapped between calls instead of going back
+// at every synchronise (the default pool's behaviour, which made each call
+// map its buffers again).  Freed with cudaFreeAsync like any pool block.
+cudaError_t scratch_malloc(void** p, size_t bytes, cudaStream_t stream);
+
+// That pool on the current device (created if needed), or nullptr.
+cudaMemPool_t scratch_pool();
+
 }  // namespace lya

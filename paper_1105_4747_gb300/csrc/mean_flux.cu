@@ -591,6 +591,37 @@ int sm_count()
     return v;
 }
 
+cudaMemPool_t scratch_pool()
+{
+    constexpr int kMaxDev = 64;
+    static std::mutex mu;
+    static cudaMemPool_t pools[kMaxDev] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        unsigned long long keep = ~0ull;                      // never hand memory back on a synchronise
+        (void)cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        pools[dev] = pool;
+    }
+    return pools[dev];
+}
+
+cudaError_t scratch_malloc(void** p, size_t bytes, cudaStream_t stream)
+{
+    cudaMemPool_t pool = scratch_pool();
+    return pool ? cudaMallocFromPoolAsync(p, bytes, pool, stream) : cudaMallocAsync(p, bytes, stream);
+}
+
 size_t max_dynamic_smem()
 {
     int dev = 0, v = 0;
@@ -706,10 +737,10 @@ lya_status mean_flux_solve(const float* tau, int64_t n, double target, double to
     Partial* part = nullptr;
     StatPart* spart = nullptr;
     StatsOut* sout = nullptr;
-    cudaError_t err = cudaMallocAsync((void**)&st, sizeof(MFState), stream);
-    if (err == cudaSuccess) err = cudaMallocAsync((void**)&part, sizeof(Partial) * grid, stream);
-    if (err == cudaSuccess && stats_out) err = cudaMallocAsync((void**)&spart, sizeof(StatPart) * grid, stream);
-    if (err == cudaSuccess && stats_out) err = cudaMallocAsync((void**)&sout, sizeof(StatsOut), stream);
+    cudaError_t err = scratch_malloc((void**)&st, sizeof(MFState), stream);
+    if (err == cudaSuccess) err = scratch_malloc((void**)&part, sizeof(Partial) * grid, stream);
+    if (err == cudaSuccess && stats_out) err = scratch_malloc((void**)&spart, sizeof(StatPart) * grid, stream);
+    if (err == cudaSuccess && stats_out) err = scratch_malloc((void**)&sout, sizeof(StatsOut), stream);
     lya_status result = err == cudaSuccess
         ? solve_on_scratch(tau, n, target, tol, max_iter, A_out, flux_out, st, part, grid, stream, spart, sout,
                            stats_out)
@@ -729,8 +760,8 @@ lya_status flux_stats_run(const float* flux, int64_t n, lya_flux_stats_t* out, c
     double* part = nullptr;
     StatsOut h{};
     cudaError_t err = cudaSuccess;
-    LYA_TRY(cudaMallocAsync((void**)&d, sizeof(StatsOut), stream));
-    LYA_TRY(cudaMallocAsync((void**)&part, sizeof(double) * 2 * grid, stream));
+    LYA_TRY(scratch_malloc((void**)&d, sizeof(StatsOut), stream));
+    LYA_TRY(scratch_malloc((void**)&part, sizeof(double) * 2 * grid, stream));
     LYA_TRY(cudaMemsetAsync(d, 0, sizeof(StatsOut), stream));
     stats_kernel<<<grid, kThreads, 0, stream>>>(flux, n, d, part);
     count_launch();
@@ -927,8 +958,8 @@ lya_status run_sums(int64_t n, double* out3, cudaStream_t stream, Launch launch)
     Partial* part = nullptr;
     SumsOut* d = nullptr;
     SumsOut h{};
-    cudaError_t e = cudaMallocAsync((void**)&part, sizeof(Partial) * grid, stream);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&d, sizeof(SumsOut), stream);
+    cudaError_t e = scratch_malloc((void**)&part, sizeof(Partial) * grid, stream);
+    if (e == cudaSuccess) e = scratch_malloc((void**)&d, sizeof(SumsOut), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, sizeof(SumsOut), stream);
     if (e == cudaSuccess) {
         launch(grid, part, d);

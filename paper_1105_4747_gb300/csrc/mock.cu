@@ -223,7 +223,7 @@ lya_status mock_spectra_run(const float* flux, int64_t n_skewers, int n_pix, int
     float* w = nullptr;
     cudaError_t e = cudaSuccess;
     if (W > 0) {
-        e = cudaMallocAsync((void**)&w, sizeof(float) * (2 * W + 1), stream);
+        e = scratch_malloc((void**)&w, sizeof(float) * (2 * W + 1), stream);
         if (e == cudaSuccess) {
             mock_weights_kernel<<<1, kMockThreads, 0, stream>>>(W, du_over_sigma, w);
             count_launch();
@@ -256,8 +256,8 @@ lya_status flux_power_run(const float* flux, int64_t n_skewers, int n_pix, doubl
     const int grid_sum = (int)std::min<long long>((n + kThreads - 1) / kThreads, 8LL * sm_count());
     double* d = nullptr;       // [0] sum of F, [1..H] power totals, then partials
     unsigned int* ticket = nullptr;
-    cudaError_t e = cudaMallocAsync((void**)&d, sizeof(double) * (1 + H + grid_sum), stream);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&ticket, sizeof(unsigned int), stream);
+    cudaError_t e = scratch_malloc((void**)&d, sizeof(double) * (1 + H + grid_sum), stream);
+    if (e == cudaSuccess) e = scratch_malloc((void**)&ticket, sizeof(unsigned int), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, sizeof(double) * (1 + H), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ticket, 0, sizeof(unsigned int), stream);
     if (e == cudaSuccess) {

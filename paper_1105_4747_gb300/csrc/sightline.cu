@@ -133,8 +133,8 @@ lya_status sightlines_run(int n_pix, double box, double k_j, double sigma, doubl
     const int H = n_pix / 2 - 1;
     float* table = nullptr;
     double* consts = nullptr;
-    cudaError_t e = cudaMallocAsync((void**)&table, sizeof(float) * 3 * (size_t)(H > 0 ? H : 1), stream);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&consts, 2 * sizeof(double), stream);
+    cudaError_t e = scratch_malloc((void**)&table, sizeof(float) * 3 * (size_t)(H > 0 ? H : 1), stream);
+    if (e == cudaSuccess) e = scratch_malloc((void**)&consts, 2 * sizeof(double), stream);
     if (e == cudaSuccess) {
         sightline_modes_kernel<<<1, kThreads, 0, stream>>>(n_pix, box, k_j, sigma, k_f, aH, table, consts);
         count_launch();

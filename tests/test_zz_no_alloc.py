@@ -4,9 +4,10 @@ lya_rescale_mean_flux_noalloc serves callers that cannot allocate device
 memory (plug-ins that must not allocate after start-up, services whose memory
 budget is spent); its scratch is a fixed device array inside liblya.  Besides
 the answers, the test reads the high watermark of the device's default
-stream-ordered memory pool (the pool the library's allocating calls draw
-from) through the driver API: it must not grow during a no-alloc call, and it
-does grow during the allocating call on the same input.  This file is named to be
+stream-ordered memory pool through the driver API and that of the
+library's own scratch pool (lya_scratch_high_watermark, the pool the
+allocating calls draw from): neither grows during a no-alloc call, and the
+scratch pool's does during the allocating call on the same input.  This file is named to be
 collected last, so a run that stops at the first failure has run every other
 test before it.
 """
@@ -95,15 +96,22 @@ def test_noalloc_draws_nothing_from_the_memory_pool(lya):
     for _ in range(2):
         reset()
         base = read()
+        lib_base = lya.scratch_high_watermark(reset=True)
+        lib_base = lya.scratch_high_watermark()
         lya.rescale_mean_flux_noalloc(tau, 0.75, F)
         torch.cuda.synchronize()
         assert read() == base
-    # the allocating call on the same input does draw from the pool
+        assert lya.scratch_high_watermark() == lib_base
+    # the allocating call on the same input does draw from the library's pool
+    # (and not from the default one)
     reset()
     base = read()
+    lya.scratch_high_watermark(reset=True)
+    lib_base = lya.scratch_high_watermark()
     lya.rescale_mean_flux(tau, 0.75, flux_out=F)
     torch.cuda.synchronize()
-    assert read() > base
+    assert lya.scratch_high_watermark() > lib_base
+    assert read() == base
 
 
 def test_noalloc_errors_match(lya):
