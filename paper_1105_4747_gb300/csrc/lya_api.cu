@@ -84,13 +84,12 @@ uint64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); 
 
 namespace {
 
-lya_status check_and_record(lya_field f, cudaStream_t s)
+// The finished check's totals read back on s (after everything before it on
+// s), and the field's extents recorded for the window bound.
+lya_status record_check(lya_field f, cudaStream_t s)
 {
-    const int64_t n = f->desc.n_skewers * f->desc.n_pix;
-    cudaError_t e = lya::launch_field_check(f->rho, f->vpec, f->temp, n, f->d_check, s);
-    if (e != cudaSuccess) return from_cuda(e);
     lya::FieldCheck h{};
-    e = cudaMemcpyAsync(&h, f->d_check, sizeof(h), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaMemcpyAsync(&h, f->d_check, sizeof(h), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return from_cuda(e);
     if (h.bad_rho || h.bad_vpec || h.bad_temp) return LYA_EINVAL;
@@ -98,6 +97,19 @@ lya_status check_and_record(lya_field f, cudaStream_t s)
     std::memcpy(&f->rho_max, &h.rho_max_bits, sizeof(float));
     std::memcpy(&f->rho_minpos, &h.rho_minpos_bits, sizeof(float));
     return LYA_OK;
+}
+
+// The whole field checked at once.  The host first waits for the work
+// already on s (the copies in), so the check kernel is never queued behind
+// a copy: a kernel parked behind a long copy can hold up other streams'
+// kernels queued after it on the same hardware queue.
+lya_status check_and_record(lya_field f, cudaStream_t s)
+{
+    const int64_t n = f->desc.n_skewers * f->desc.n_pix;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = lya::launch_field_check(f->rho, f->vpec, f->temp, n, f->d_check, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    return record_check(f, s);
 }
 
 lya_status copy_in(lya_field f, const float* rho, const float* vpec, const float* temp, int src,
@@ -111,9 +123,67 @@ lya_status copy_in(lya_field f, const float* rho, const float* vpec, const float
     return from_cuda(e);
 }
 
+// Copies a host field in and validates it.  The copies go in kLoadPieces
+// pieces of whole skewers on s, all enqueued at once; the host waits for
+// each piece's event and then launches that piece's check on the field's
+// check stream, so every check runs while later pieces are still crossing
+// the link (the link idles only for the last piece's check), and no check
+// kernel ever waits in a queue for a copy (see check_and_record).  Device
+// sources (fast copies) take one copy per array and one check.
+constexpr int kLoadPieces = 8;
+
+lya_status load_checked(lya_field f, const float* rho, const float* vpec, const float* temp, int src,
+                        cudaStream_t s)
+{
+    const int64_t R = f->desc.n_skewers, N = f->desc.n_pix;
+    if (src != LYA_SRC_HOST || R < kLoadPieces) {
+        const lya_status st = copy_in(f, rho, vpec, temp, src, s);
+        return st != LYA_OK ? st : check_and_record(f, s);
+    }
+    cudaError_t e = cudaSuccess;
+    if (!f->check_stream) {
+        e = cudaStreamCreateWithFlags(&f->check_stream, cudaStreamNonBlocking);
+        for (int k = 0; e == cudaSuccess && k < kLoadPieces; ++k)
+            e = cudaEventCreateWithFlags(&f->piece_ev[k], cudaEventDisableTiming);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    cudaStream_t c = f->check_stream;
+    e = lya::launch_field_check_init(f->d_check, c);
+    int64_t off[kLoadPieces], cnt[kLoadPieces];
+    for (int k = 0; e == cudaSuccess && k < kLoadPieces; ++k) {
+        const int64_t r0 = R * k / kLoadPieces, r1 = R * (k + 1) / kLoadPieces;
+        off[k] = r0 * N;
+        cnt[k] = (r1 - r0) * N;
+        const size_t bytes = sizeof(float) * (size_t)cnt[k];
+        e = cudaMemcpyAsync(f->rho + off[k], rho + off[k], bytes, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(f->vpec + off[k], vpec + off[k], bytes, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && f->temp)
+            e = cudaMemcpyAsync(f->temp + off[k], temp + off[k], bytes, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaEventRecord(f->piece_ev[k], s);
+    }
+    for (int k = 0; e == cudaSuccess && k < kLoadPieces; ++k) {
+        e = cudaEventSynchronize(f->piece_ev[k]);          // piece k is on the device
+        if (e == cudaSuccess)
+            e = lya::launch_field_check_range(f->rho + off[k], f->vpec + off[k],
+                                              f->temp ? f->temp + off[k] : nullptr, cnt[k], f->d_check, c);
+    }
+    if (e != cudaSuccess) {
+        (void)cudaStreamSynchronize(s);
+        (void)cudaStreamSynchronize(c);
+        return from_cuda(e);
+    }
+    return record_check(f, c);       // every copy on s has landed (each piece's event was waited for)
+}
+
 void release(lya_field f)
 {
     if (!f) return;
+    if (f->check_stream) {
+        cudaStreamSynchronize(f->check_stream);
+        for (cudaEvent_t ev : f->piece_ev)
+            if (ev) cudaEventDestroy(ev);
+        cudaStreamDestroy(f->check_stream);
+    }
     if (f->owned) {
         cudaFree(f->rho);
         cudaFree(f->vpec);
@@ -287,10 +357,9 @@ lya_status lya_create_field(const lya_field_desc* desc, const float* rho, const 
         if (e == cudaSuccess) e = cudaMalloc((void**)&f->vpec, bytes);
         if (e == cudaSuccess && temp) e = cudaMalloc((void**)&f->temp, bytes);
         if (e != cudaSuccess) { release(f); return from_cuda(e); }
-        lya_status st = copy_in(f, rho, vpec, temp, src, s);
-        if (st != LYA_OK) { release(f); return st; }
     }
-    lya_status st = check_and_record(f, s);
+    const lya_status st = src == LYA_SRC_DEVICE_BORROW ? check_and_record(f, s)
+                                                       : load_checked(f, rho, vpec, temp, src, s);
     if (st != LYA_OK) { release(f); return st; }
     *out = f;
     return LYA_OK;
@@ -302,10 +371,7 @@ lya_status lya_field_load(lya_field f, const float* rho, const float* vpec, cons
     if (!f || !rho || !vpec || !f->owned) return LYA_EINVAL;
     if ((f->temp != nullptr) != (temp != nullptr)) return LYA_EINVAL;
     if (src != LYA_SRC_HOST && src != LYA_SRC_DEVICE_COPY) return LYA_EINVAL;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    lya_status st = copy_in(f, rho, vpec, temp, src, s);
-    if (st != LYA_OK) return st;
-    return check_and_record(f, s);
+    return load_checked(f, rho, vpec, temp, src, static_cast<cudaStream_t>(stream));
 }
 
 lya_status lya_destroy_field(lya_field f)

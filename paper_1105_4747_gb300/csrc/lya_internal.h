@@ -26,6 +26,10 @@ struct lya_field_s {
     float rho_minpos = 0.f;          // smallest rho > 0
     int device = 0;
     std::atomic<int> users{0};       // server requests not yet finished
+    // chunked loads from host memory: the check runs on its own stream, each
+    // piece once the host has seen its copies' event (created at the first load)
+    cudaStream_t check_stream = nullptr;
+    cudaEvent_t piece_ev[8] = {};
 };
 
 namespace lya {
@@ -151,6 +155,11 @@ struct FieldCheck {
 };
 cudaError_t launch_field_check(const float* rho, const float* vpec, const float* temp,
                                int64_t n, FieldCheck* d_out, cudaStream_t stream);
+// The same in parts: set the totals empty, then check any number of ranges
+// into them (atomics), e.g. each piece of a chunked load as it lands.
+cudaError_t launch_field_check_init(FieldCheck* d_out, cudaStream_t stream);
+cudaError_t launch_field_check_range(const float* rho, const float* vpec, const float* temp,
+                                     int64_t n, FieldCheck* d_out, cudaStream_t stream);
 
 // Count one kernel launch (lya_kernel_launches).
 void count_launch(int n = 1);

@@ -507,6 +507,19 @@ __global__ void __launch_bounds__(kThreads) stats_kernel(const float* __restrict
 }
 
 // ---- field validation ---------------------------------------------------------------
+// The check's totals start empty (no flags, maxima 0, the smallest positive
+// rho at +inf); field_check_kernel accumulates into them with atomics, so a
+// field may be checked in pieces.
+__global__ void field_check_init_kernel(FieldCheck* out)
+{
+    if (threadIdx.x == 0) {
+        out->bad_rho = out->bad_vpec = out->bad_temp = 0ull;
+        out->temp_max_bits = 0u;
+        out->rho_max_bits = 0u;
+        out->rho_minpos_bits = 0x7f800000u;           // +inf
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) field_check_kernel(const float* __restrict__ rho,
                                                              const float* __restrict__ v,
                                                              const float* __restrict__ T, long long n,
@@ -630,17 +643,28 @@ size_t max_dynamic_smem()
     return (size_t)v;
 }
 
-cudaError_t launch_field_check(const float* rho, const float* vpec, const float* temp, int64_t n,
-                               FieldCheck* d_out, cudaStream_t stream)
+cudaError_t launch_field_check_init(FieldCheck* d_out, cudaStream_t stream)
 {
-    FieldCheck init{};
-    init.rho_minpos_bits = 0x7f800000u;     // +inf
-    cudaError_t e = cudaMemcpyAsync(d_out, &init, sizeof(FieldCheck), cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);   // init is a stack value
-    if (e != cudaSuccess || n == 0) return e;
+    field_check_init_kernel<<<1, 32, 0, stream>>>(d_out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_check_range(const float* rho, const float* vpec, const float* temp, int64_t n,
+                                     FieldCheck* d_out, cudaStream_t stream)
+{
+    if (n == 0) return cudaSuccess;
     field_check_kernel<<<grid_for(n), kThreads, 0, stream>>>(rho, vpec, temp, n, d_out);
     count_launch();
     return cudaGetLastError();
+}
+
+cudaError_t launch_field_check(const float* rho, const float* vpec, const float* temp, int64_t n,
+                               FieldCheck* d_out, cudaStream_t stream)
+{
+    cudaError_t e = launch_field_check_init(d_out, stream);
+    if (e == cudaSuccess) e = launch_field_check_range(rho, vpec, temp, n, d_out, stream);
+    return e;
 }
 
 #define LYA_TRY(call)                                   \

@@ -245,6 +245,44 @@ def test_field_rejects_out_of_domain_values(lya):
             make_field(lya, spec, r, vv, tt)
 
 
+def test_chunked_host_load_checks_every_piece(lya):
+    """A host field of >= 8 skewers is copied in eight pieces, each validated
+    as it lands: a bad value in the first or the last piece is refused, on
+    creation and on a load; a load of a hotter field records its extents (the
+    window bound follows them), so the loaded field extracts as a fresh one."""
+    import torch
+    spec = ls.TINY_20MPC
+    n = 64
+    rho, v, t = ls.skewers(spec, np.arange(n))
+    for row in (0, n - 1):
+        for mut in ("rho_nan", "v_inf", "t_zero"):
+            r, vv, tt = rho.copy(), v.copy(), t.copy()
+            if mut == "rho_nan":
+                r[row, 7] = np.nan
+            elif mut == "v_inf":
+                vv[row, 3] = np.inf
+            else:
+                tt[row, 11] = 0.0
+            with pytest.raises(lya.LyaError):
+                make_field(lya, spec, r, vv, tt)
+            f = make_field(lya, spec, rho, v, t)
+            with pytest.raises(lya.LyaError):
+                f.load(r, vv, tt)
+            f.close()
+    # a hotter field loaded over a cool one: the window grows with its T_max
+    f = make_field(lya, spec, rho, v, t)
+    hot = (t * 25.0).astype(np.float32)
+    f.load(rho, v, hot)
+    fresh = make_field(lya, spec, rho, v, hot)
+    a = lya.extract_skewers(f, lya.ExtractParams())
+    b = lya.extract_skewers(fresh, lya.ExtractParams())
+    torch.cuda.synchronize()
+    rel = ((a - b).abs() / b.abs().clamp_min(1e-30)).max().item()
+    assert rel <= 3e-7
+    f.close()
+    fresh.close()
+
+
 # ----------------------------------------------------------------------------
 # mean-flux rescaling and statistics
 # ----------------------------------------------------------------------------
