@@ -45,15 +45,15 @@ ALG_BYTES_PER_PX = 16          # rho, vpec, T read (12 B) + tau written (4 B)
 # scaled by the number of skewers, with the SHA-1 of the kernel source each
 # was taken on: reported as null once paper_1105_4747_gb300/csrc/tau_extract.cu
 # differs from it.
-TAU_DRAM_PROFILE = {"gpc": ((402.951168e6 + 112.1984e6) / 8192, "88b1ac9fac8321f603415f16357f49a982d64067"),
-                    "grid1536": ((2.416071936e9 + 0.759599616e9) / 131072, "88b1ac9fac8321f603415f16357f49a982d64067")}
+TAU_DRAM_PROFILE = {"gpc": ((402.798592e6 + 113.191424e6) / 8192, "c274fd95e764757eb255cf1ac4ecf05cf9974d4f"),
+                    "grid1536": ((2.416186112e9 + 0.75963264e9) / 131072, "c274fd95e764757eb255cf1ac4ecf05cf9974d4f")}
 
 
 # ncu pipe utilisation of the same tau-kernel launch as TAU_DRAM_PROFILE["gpc"]
 # (8,192 skewers, --set full, profiles/tau_tile_kernel_gpc_8192x4096.md), with
 # the code hash it was taken on: reported as null once the kernel differs.
 TAU_PIPE_PROFILE = {"gpc": ({"fma_pct": 19.4, "xu_pct": 20.4, "alu_pct": 46.1, "lsu_pct": 19.3,
-                             "issue_active_pct": 67.6}, "88b1ac9fac8321f603415f16357f49a982d64067")}
+                             "issue_active_pct": 67.5}, "c274fd95e764757eb255cf1ac4ecf05cf9974d4f")}
 FP32_OPS_PER_PAIR = 6          # per pair of the sum: argument (2), square, exponent scale, weight, add
 KB_J_PER_K = 1.380649e-23
 M_H_KG = 1.6735575e-27
