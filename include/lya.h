@@ -177,10 +177,15 @@ lya_status lya_extract_skewers(lya_field field, const lya_extract_params* params
 /*
  * Mean-flux rescaling (Sec. 2.3): find A with <exp(-A tau)> = target over all
  * n device values tau (every pixel of every skewer, equally weighted).
- * Safeguarded Newton in FP64 from A0 = -ln(target)/<tau>, stopping when
- * |<exp(-A tau)> - target| <= tol or the step stalls at FP64 resolution.
- * *A_out receives A (host).  If flux_out (device, n floats) is not NULL it
- * receives F = exp(-A tau).  Returns LYA_EINVAL if target is not in (0,1),
+ * A safeguarded Halley/Newton/bisection iteration on the device, started from
+ * a sample of tau, with <exp(-A tau)> evaluated to ~1e-13 (double-float
+ * exponentials, FP64 sums); it stops when |<exp(-A tau)> - target| <= tol, or
+ * when its last Newton step is certified by Taylor's bound to land within
+ * tol, or when the step stalls at FP64 resolution.  *A_out receives A (host).
+ * If flux_out (device, n floats) is not NULL it receives F = exp(-A tau) in
+ * FP32, within 6e-8 plus one rounding of exp(-A tau) at the returned A
+ * (written by the last evaluation pass when its step moved A little enough,
+ * else by a flux pass at the final A).  Returns LYA_EINVAL if target is not in (0,1),
  * tau holds a negative or non-finite value or all tau are 0; LYA_ENOCONV if
  * no A reaches the target (too many tau = 0) or max_iter is exhausted.
  * Synchronises the stream.
@@ -215,9 +220,9 @@ lya_status lya_rescale_mean_flux_noalloc(const float* tau, int64_t n, double tar
 
 /*
  * lya_rescale_mean_flux followed by lya_flux_stats of the F it writes, with
- * the statistics gathered in the root-find's final flux pass instead of a
- * separate read of F (Sec. 2.3, Sec. 5.2).  flux_out may be NULL (the
- * statistics are still those of exp(-A tau) in FP32).  Arguments, results and
+ * the statistics gathered in the pass that writes F instead of a separate
+ * read of F (Sec. 2.3, Sec. 5.2).  flux_out may be NULL (the statistics are
+ * still those of exp(-A tau) in FP32).  Arguments, results and
  * errors are those of the two calls; stats_out must not be NULL.
  * Synchronises the stream.
  */
