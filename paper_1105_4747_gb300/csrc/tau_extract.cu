@@ -1381,10 +1381,11 @@ static cudaError_t launch_kernel(K kernel, const TauLaunch& L0, size_t smem, int
 }
 
 // Inputs staged by bulk copies for rows of 2,048 pixels or more (n_pix % 4 ==
-// 0: rows 16-byte aligned, since fields are); measured on GB300 at 65,536 x
-// 4,096 px: 3.92 ms staged against 3.96 ms with vector loads, and on 1536^3
-// grid rows 50.8 ms against 50.0 ms, hence the threshold.  LYA_TILE_STAGE=0/1
-// in the environment forces either (diagnostics).
+// 0: rows 16-byte aligned, since fields are); measured on GB300 on 16,384 x
+// 4,096 px: 0.953 ms staged against 0.958 ms with vector loads, and on
+// 262,144 rows of 1,536 px 5.10 ms staged against 4.87 ms, hence the
+// threshold.  LYA_TILE_STAGE=0/1 in the environment forces either
+// (diagnostics).
 static bool stage_inputs(const TauLaunch& L)
 {
     const char* env = std::getenv("LYA_TILE_STAGE");
