@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kThreads) mf_state_init_kernel(MFState* st, do
 // largest tau: t + 0 maps -0 to +0, and the largest of those float bits as
 // unsigned is above 0x7f7fffff exactly when some value is negative, infinite
 // or NaN, else it is the bits of the largest tau.
-__global__ void __launch_bounds__(kThreads) mf_newton_kernel(const float* __restrict__ tau, long long n,
+__global__ void __launch_bounds__(kThreads, 6) mf_newton_kernel(const float* __restrict__ tau, long long n,
                                                            MFState* st, Partial* part)
 {
     if (st->done) return;
@@ -583,6 +583,17 @@ int grid_for(long long n)
     return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
+// The fast Halley pass's grid: six CTAs per SM (it holds 40 registers at that
+// bound), so more of its loads are in flight than at the four of the other
+// passes; at most `cap` CTAs (the partials the scratch holds).
+int fast_grid_for(long long n, int cap)
+{
+    const long long want = (n + kThreads - 1) / kThreads;
+    long long g = 6LL * sm_count();
+    if (want < g) g = want > 0 ? want : 1;
+    return (int)(g < cap ? g : cap);
+}
+
 }  // namespace
 
 // SM count of the current device, cached per device (a relaxed atomic per
@@ -682,8 +693,8 @@ namespace {
 // round.
 static lya_status solve_on_scratch(const float* tau, int64_t n, double target, double tol, int max_iter,
                                    double* A_out, float* flux_out, MFState* st, Partial* part, int grid,
-                                   cudaStream_t stream, StatPart* spart = nullptr, StatsOut* sout = nullptr,
-                                   lya_flux_stats_t* stats_out = nullptr)
+                                   int fast_grid, cudaStream_t stream, StatPart* spart = nullptr,
+                                   StatsOut* sout = nullptr, lya_flux_stats_t* stats_out = nullptr)
 {
     static_assert(sizeof(MFState) % 8 == 0, "state layout");
     MFState hs{};                                   // host copy of the state's header (no heap allocation)
@@ -704,7 +715,7 @@ static lya_status solve_on_scratch(const float* tau, int64_t n, double target, d
         // a fast (MUFU) Halley pass, a precise one that writes F at its A, then
         // the flux pass at the final A, which leaves at once when the precise
         // pass's F is final
-        mf_newton_kernel<<<grid, kThreads, 0, stream>>>(tau, n, st, part);
+        mf_newton_kernel<<<fast_grid, kThreads, 0, stream>>>(tau, n, st, part);
         count_launch();
         err = cudaGetLastError();
         if (err == cudaSuccess) {
@@ -757,17 +768,19 @@ lya_status mean_flux_solve(const float* tau, int64_t n, double target, double to
                            double* A_out, float* flux_out, cudaStream_t stream, lya_flux_stats_t* stats_out)
 {
     const int grid = grid_for(n);
+    const int fast_grid = fast_grid_for(n, 1 << 30);
     MFState* st = nullptr;
     Partial* part = nullptr;
     StatPart* spart = nullptr;
     StatsOut* sout = nullptr;
     cudaError_t err = scratch_malloc((void**)&st, sizeof(MFState), stream);
-    if (err == cudaSuccess) err = scratch_malloc((void**)&part, sizeof(Partial) * grid, stream);
+    if (err == cudaSuccess)
+        err = scratch_malloc((void**)&part, sizeof(Partial) * (grid > fast_grid ? grid : fast_grid), stream);
     if (err == cudaSuccess && stats_out) err = scratch_malloc((void**)&spart, sizeof(StatPart) * grid, stream);
     if (err == cudaSuccess && stats_out) err = scratch_malloc((void**)&sout, sizeof(StatsOut), stream);
     lya_status result = err == cudaSuccess
-        ? solve_on_scratch(tau, n, target, tol, max_iter, A_out, flux_out, st, part, grid, stream, spart, sout,
-                           stats_out)
+        ? solve_on_scratch(tau, n, target, tol, max_iter, A_out, flux_out, st, part, grid, fast_grid, stream,
+                           spart, sout, stats_out)
         : (err == cudaErrorMemoryAllocation ? LYA_ENOMEM : LYA_ECUDA);
     if (st) cudaFreeAsync(st, stream);
     if (part) cudaFreeAsync(part, stream);
@@ -875,7 +888,8 @@ lya_status mean_flux_solve_noalloc(const float* tau, int64_t n, double target, d
     if (kNoAllocStateBytes + (size_t)grid * sizeof(Partial) > kNoAllocScratchBytes) return LYA_EINVAL;
     MFState* st = static_cast<MFState*>(scratch);
     Partial* part = reinterpret_cast<Partial*>(static_cast<unsigned char*>(scratch) + kNoAllocStateBytes);
-    return solve_on_scratch(tau, n, target, tol, max_iter, A_out, flux_out, st, part, grid, stream);
+    return solve_on_scratch(tau, n, target, tol, max_iter, A_out, flux_out, st, part, grid,
+                            fast_grid_for(n, kNoAllocMaxBlocks), stream);
 }
 
 }  // namespace lya
