@@ -58,14 +58,23 @@ __global__ void __launch_bounds__(kThreads) mf_sample_kernel(const float* __rest
     KahanF32 s;
     unsigned int z = 0, cnt = 0;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x, nthr = (long long)gridDim.x * blockDim.x;
-    for (long long k = tid; k < ns; k += nthr) {
-        const float t = tau[k * (smask + 1)];
-        if (!(t >= 0.f) || !isfinite(t)) continue;
+    auto take = [&](float t) {
+        if (!(t >= 0.f) || !isfinite(t)) return;
         s.add(t);
         ++cnt;
         z += (t == 0.f);
         atomicAdd(&h_s[t == 0.f ? kHistBins : hist_bin(t)], 1u);
+    };
+    // four strided loads in flight per thread, then their values
+    long long k = tid;
+    for (; k + 3 * nthr < ns; k += 4 * nthr) {
+        float t[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) t[u] = tau[(k + u * nthr) * (smask + 1)];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) take(t[u]);
     }
+    for (; k < ns; k += nthr) take(tau[k * (smask + 1)]);
     __shared__ double sh[3][32];
     double v[3] = {(double)s.value(), (double)z, (double)cnt};
     block_sum<3>(v, sh);
