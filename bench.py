@@ -579,10 +579,22 @@ def run_e2e(lya, torch, field, spec, S, params, target, rho, v, t, tau, F, n_ste
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     dt = max_over_ranks(dt, world)
+    # the one-way bandwidth of these very host buffers (best of three 1-array
+    # copies), beside the link measured on separate buffers: tells a slow
+    # placement of the step's buffers apart from a slow pipeline
+    dst = torch.empty(rho_h.shape, dtype=torch.float32, device="cuda")
+    best = 0.0
+    for _ in range(3):
+        torch.cuda.synchronize()
+        c0 = time.perf_counter()
+        dst.copy_(rho_h, non_blocking=True)
+        torch.cuda.synchronize()
+        best = max(best, rho_h.numel() * 4 / (time.perf_counter() - c0) / 1e9)
+    del dst
     fields[1].close()
     return {"value": world * n_steps * n_px / dt, "unit": UNIT,
             "h2d_bytes_per_step": 3 * n_px * 4, "d2h_bytes_per_step": n_px * 4,
-            "ms_per_step": 1e3 * dt / n_steps, "steps": n_steps,
+            "ms_per_step": 1e3 * dt / n_steps, "steps": n_steps, "buffers_h2d_gbs": best,
             "timing": "host wall clock around all steps, device synchronised at both ends",
             "pipeline": "two device fields and two F buffers: H2D of step k+1 and D2H of step k-1 overlap step k"}
 
